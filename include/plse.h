@@ -1,0 +1,195 @@
+/*
+ * plse.h -- C ABI of the GB300 (sm_103a) hot path of MPMA, the massively
+ * parallel memetic algorithm for partial Latin square extension (PLSE) of
+ * Goudet & Hao, arXiv 2103.10453.
+ *
+ * All compute runs in hand-written CUDA kernels inside libplse.so.  Signatures
+ * use plain pointers and sizes only.  Unless stated otherwise:
+ *   - "host" buffers are caller-owned CPU memory, read or written before the
+ *     call returns;
+ *   - "device" buffers are caller-owned GPU memory on the current device
+ *     (e.g. torch tensors), accessed in stream order on `stream`;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     calls taking a stream are asynchronous with respect to the host;
+ *   - every call returns PLSE_OK (0) or a negative PLSE_E* code, and on error
+ *     leaves outputs unspecified; plse_last_error_detail() explains the last
+ *     error of a handle.
+ *
+ * Colourings are uint8 arrays [count][nv] (row-major by individual) over the
+ * reduced vertices of the instance, in row-major cell order; colour 0 means
+ * "uncoloured", colour k in 1..n means symbol k (Sec. 2.1).
+ * Random numbers are Philox4x32-10 blocks keyed by `seed` with the counter
+ * (iteration or vertex block, individual, generation<<8 | purpose<<4 | phase, 0),
+ * so every result is a deterministic function of its arguments.
+ */
+#ifndef PLSE_H
+#define PLSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes --------------------------------------------------------- */
+#define PLSE_OK          0
+#define PLSE_EINVAL     -1   /* invalid argument or invalid grid               */
+#define PLSE_ENOMEM     -2   /* host or device allocation failed               */
+#define PLSE_ECUDA      -3   /* CUDA runtime error                             */
+#define PLSE_EBUSY      -4   /* admission refused: not enough device memory    */
+#define PLSE_ECANCELLED -5   /* cancelled through plse_cancel                  */
+#define PLSE_ENOTSUP    -6   /* parameter combination not supported            */
+#define PLSE_ECHECK     -7   /* a device-side bound check failed               */
+
+typedef struct plse_instance *plse_handle;
+
+/* Algorithm parameters: Table 1 of the paper and Sec. 3.3, as integers. */
+typedef struct {
+    int32_t alpha_num, alpha_den;  /* tabu tenure factor alpha = 6/10            */
+    int32_t tenure_rand;           /* L uniform in [0, tenure_rand) = [0, 9]     */
+    int32_t phase1_phi2;           /* 2*phi of phase 1 (phi = 0.5 -> 1)          */
+    int32_t phase2_phi2_per_v;     /* 2*phi of phase 2 per |V| (phi = |V| -> 2)  */
+    int32_t phase2_iter_per_v;     /* phase-2 iterations per |V| (2)             */
+    int32_t spacing_gamma;         /* Alg. 4 spacing D > |V|/gamma (10)          */
+    int32_t beta;                  /* AUX parameter beta (20)                    */
+    int32_t mode;                  /* PLSE_MODE_PLITS or PLSE_MODE_PARTIALCOL    */
+    int32_t matching;              /* PLSE_MATCH_NEAREST or PLSE_MATCH_RANDOM    */
+    int32_t crossover;             /* PLSE_XOVER_AUX or PLSE_XOVER_UX            */
+    int32_t tested_cap;            /* tested-partner list capacity, 1..256 (64)  */
+} plse_params;
+
+#define PLSE_MODE_PLITS       0    /* two-phase tabu search, Sec. 3.3            */
+#define PLSE_MODE_PARTIALCOL  1    /* Partial-MPMA local search, Sec. 3.7        */
+#define PLSE_MATCH_NEAREST    0    /* nearest untested partner, Sec. 3.5.1       */
+#define PLSE_MATCH_RANDOM     1    /* random partner (ablation of Sec. 5.3)      */
+#define PLSE_XOVER_AUX        0    /* asymmetric uniform crossover, Eq. 10       */
+#define PLSE_XOVER_UX         1    /* uniform crossover, p_ij = 1/2              */
+
+/* Work counters of tabu walks (identical to the CPU oracle's on the same
+ * trajectory): iterations executed, moves applied, sum of |V0 u C(S)| over
+ * iterations, sum of scanned (v, j) pairs, sum of deg(v*) over moves,
+ * strict improvements of the walk's best, neighbours uncoloured (PartialCol). */
+typedef struct {
+    int64_t iterations, moves, cand, pairs, deg, improvements, uncolored;
+} plse_walk_stats;
+
+typedef struct {
+    int32_t generations;      /* generations executed (early stop at the bound) */
+    int32_t best_f;           /* f(S*): uncoloured reduced vertices of S*       */
+    plse_walk_stats walks;    /* summed over every walk of the run              */
+    double  ms_total;         /* device time of the whole run (CUDA events)     */
+    double  ms_local_search;  /* device time of the local-search launches       */
+} plse_solve_stats;
+
+/* ---- instance -------------------------------------------------------------
+ * plse_create -- Sec. 2.1-2.2, Alg. 1.  `grid`: host int8 [n*n], row-major,
+ * 0 = empty cell, 1..n = prefilled symbol; copied, so the caller may free it on
+ * return.  Validates 1 <= n <= 127, symbols in 0..n and no symbol twice in a
+ * row or a column (partial Latin square, Sec. 1); PLSE_EINVAL otherwise.
+ * Builds the reduced graph (empty cells with D(v) != {0}), the domains D(v),
+ * l and the bound, and uploads them to the current device.  *out is written
+ * only on success.  The handle is not thread-safe: one host thread at a time. */
+int  plse_create(int n, const int8_t *grid, plse_handle *out);
+/* Frees every host and device resource of `h`; NULL is accepted. */
+void plse_destroy(plse_handle h);
+/* Static description of an error code; never NULL. */
+const char *plse_strerror(int code);
+/* Copies the last error message of `h` (NUL-terminated, truncated to len). */
+int  plse_last_error_detail(plse_handle h, char *buf, size_t len);
+/* |V| (reduced vertices), l (cells removed by Alg. 1 because D = {0}) and the
+ * upper bound n^2 - l, or n^2 - 2 when l = 1 (Sec. 2.2).  NULL outputs skipped. */
+int  plse_info(plse_handle h, int *nv, int *l, int *ub);
+
+/* Waits for `stream`, then reports PLSE_ECHECK (and clears the condition) if a
+ * kernel of an earlier call on `h` failed one of its device-side consistency
+ * checks; PLSE_OK otherwise. */
+int  plse_sync(plse_handle h, void *stream);
+
+/* ---- parameters ---------------------------------------------------------- */
+/* Table 1 defaults: alpha 6/10, L in [0,9], phi 0.5 then |V| for 2|V|
+ * iterations, gamma 10, beta 20, PLITS, nearest matching, AUX, 64 partners. */
+void plse_default_params(plse_params *p);
+int  plse_set_params(plse_handle h, const plse_params *p);
+int  plse_get_params(plse_handle h, plse_params *p);
+
+/* ---- whole solve (Alg. 2) ---------------------------------------------------
+ * Runs `generations` generations of MPMA with population `pop` (2..65535) and
+ * `iters` phase-1 tabu iterations (nbIter_TS of Sec. 3.3; phase 2 uses
+ * phase2_iter_per_v*|V|), stopping early once the bound is reached (Sec. 3.2).
+ * `best_grid`: host int8 [n*n] output = prefilled symbols + the best legal
+ * colouring S* (0 for uncoloured and removed cells).  `best_score` = number of
+ * filled cells = n^2 - l - f(S*).  Blocks until done.  Deterministic in
+ * (instance, params, pop, generations, iters, seed). */
+int  plse_solve(plse_handle h, int pop, int generations, int64_t iters, uint64_t seed,
+                int8_t *best_grid, int *best_score);
+/* As plse_solve, enqueued on `stream` (the call still blocks until the result is
+ * on the host) and returning device-timed statistics in *stats (may be NULL). */
+int  plse_solve_ex(plse_handle h, int pop, int generations, int64_t iters, uint64_t seed,
+                   void *stream, int8_t *best_grid, int *best_score,
+                   plse_solve_stats *stats);
+
+/* ---- step entry points (device buffers, asynchronous on `stream`) ---------
+ * plse_init_population -- Sec. 3.2: P[i][v] uniform over D(v)\{0}, individual
+ * index i for i < pop.  P: device uint8 [pop*nv]. */
+int  plse_init_population(plse_handle h, int pop, uint64_t seed, uint8_t *P, void *stream);
+
+/* plse_local_search -- Alg. 3 on `count` colourings.  S_in / S_out: device
+ * uint8 [count*nv] (may alias).  Walk w uses individual index ind0 + w and
+ * generation `gen` for its Philox draws.  flags: PLSE_LS_PHASE1 runs
+ * `iters` iterations with phi = 0.5 (Sec. 3.3); PLSE_LS_PHASE2 then runs
+ * phase2_iter_per_v*|V| iterations with phi = |V| from the phase-1 best;
+ * PLSE_LS_REPAIR then applies the greedy conflict removal of Sec. 3.7;
+ * PLSE_LS_PARTIALCOL (alone or with REPAIR first) runs the PartialCol tabu
+ * search of Sec. 3.7 for `iters` iterations on a legal colouring.
+ * Outputs: S_out = best colouring (S'*); f_out (device int32 [count] or NULL)
+ * = uncoloured vertices of S_out; F_out (device int64 [count] or NULL) = best
+ * value of the last phase run (2F for PLITS, f for PartialCol); stats (device
+ * plse_walk_stats [count] or NULL) = per-walk counters summed over phases.
+ * PLSE_ECHECK if a walk's device bound check failed (the walk's output is then
+ * unspecified).  Uses internal device scratch (tabu overflow tables). */
+#define PLSE_LS_PHASE1      1
+#define PLSE_LS_PHASE2      2
+#define PLSE_LS_REPAIR      4
+#define PLSE_LS_PARTIALCOL  8
+int  plse_local_search(plse_handle h, const uint8_t *S_in, uint8_t *S_out, int count,
+                       int ind0, int gen, int64_t iters, uint64_t seed, int flags,
+                       int32_t *f_out, int64_t *F_out, plse_walk_stats *stats, void *stream);
+
+/* plse_distances -- Sec. 3.4, Eq. 9: D[a*nb + b] = #v with A_a(v) != B_b(v).
+ * A: device uint8 [na*nv], B: device uint8 [nb*nv], D: device int32 [na*nb]. */
+int  plse_distances(plse_handle h, const uint8_t *A, int na, const uint8_t *B, int nb,
+                    int32_t *D, void *stream);
+
+/* plse_pop_update -- Alg. 4 over P_all = Pall[0..2p-1] (P_t first, then P'):
+ * ranks by (e, index), accepts greedily with spacing gamma*min D > |V|, fills
+ * from rejected candidates in rank order if P_all runs out.  Pall: device
+ * uint8 [2p*nv]; e: device int64 [2p] (ranking score, e.g. f + |V|*c);
+ * sel: device int32 [p] receives the chosen indices in acceptance order;
+ * filled (device int32 [1] or NULL): places taken by the fill rule.
+ * Distances are computed on the fly; nothing p x p is materialised. */
+int  plse_pop_update(plse_handle h, int p, const uint8_t *Pall, const int64_t *e,
+                     int32_t *sel, int32_t *filled, void *stream);
+
+/* plse_matching -- Sec. 3.5.1 / Alg. 5: partner[i] = nearest j != i (Hamming)
+ * whose uid is not in i's tested list (lowest index on ties; plain nearest if
+ * every partner was tested), or a random j != i with PLSE_MATCH_RANDOM.
+ * P: device uint8 [p*nv]; uid: device uint32 [p]; tested: device uint32
+ * [p*tested_cap] and tcount: device int32 [p] (updated in place: the partner's
+ * uid is appended, the oldest entry dropped when full; untouched for random
+ * matching); partner, dist: device int32 [p] (dist = D(i, partner)). */
+int  plse_matching(plse_handle h, int p, const uint8_t *P, const uint32_t *uid,
+                   uint32_t *tested, int32_t *tcount, int gen, uint64_t seed,
+                   int32_t *partner, int32_t *dist, void *stream);
+
+/* plse_crossover -- Eq. 10 / Alg. 5: O[i](v) = P[i](v) with probability
+ * p_ij = 1 - |V|/(beta*dist[i]) (clamped at 0; 1/2 for UX), else
+ * P[partner[i]](v).  P, O: device uint8 [p*nv] (must not alias);
+ * partner, dist: device int32 [p]. */
+int  plse_crossover(plse_handle h, int p, const uint8_t *P, const int32_t *partner,
+                    const int32_t *dist, int gen, uint64_t seed, uint8_t *O, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLSE_H */

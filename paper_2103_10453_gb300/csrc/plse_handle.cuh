@@ -1,0 +1,52 @@
+// plse_handle.cuh -- host-side state behind a plse_handle (library-internal).
+#pragma once
+
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "plse_internal.cuh"
+
+namespace plse {
+
+struct SolverState;   // generation-loop buffers (solve.cu)
+
+// device scratch of the local search, grown on demand and reused across calls
+struct Workspace {
+    uint32_t *G = nullptr;          // evicted tabu expiries, one table per walk slot
+    size_t G_cap = 0;
+    uint32_t *slot_clock = nullptr; // per-slot clock
+    size_t clock_cap = 0;
+    int *counters = nullptr;        // [0] walk counter, [1] error flag, [2..] spare
+    size_t counters_cap = 0;
+};
+
+}  // namespace plse
+
+struct plse_instance {
+    int n = 0, nv = 0, l = 0, ub = 0, nfixed = 0;
+    int device = 0;
+    std::vector<int8_t> grid;
+    std::vector<int32_t> cell;       // row-major cell of each reduced vertex
+    std::vector<uint16_t> rc;
+    std::vector<uint4> dom;
+    std::vector<uint8_t> ndom;
+    std::vector<int32_t> row_ptr, col_ptr;
+    std::vector<uint16_t> row_v, col_v;
+    plse_params params{};
+    void *inst_mem = nullptr;        // one device allocation holding the DevInst arrays
+    plse::DevInst di{};
+    plse::Workspace ws;
+    plse::SolverState *solver = nullptr;
+    std::string err;
+};
+
+namespace plse {
+int fail(plse_instance *h, int code, const char *fmt, ...);
+int cuda_fail(plse_instance *h, cudaError_t e, const char *where);
+int max_tenure(const plse_instance *h);
+int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
+                         int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
+                         int64_t *F_out, plse_walk_stats *stats, cudaStream_t st);
+void release_solver(plse_instance *h);
+}  // namespace plse

@@ -1,0 +1,78 @@
+// plse_internal.cuh -- shared declarations of the sm_103a kernels and the C ABI
+// layer of libplse.so.  Nothing here is visible outside the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "plse.h"
+
+namespace plse {
+
+constexpr int kMaxN = 127;            // colours 0..127 fit one 128-bit mask
+constexpr int kMaxTenure = 16383;     // relative u16 tabu clocks need T < 2^14
+constexpr int kKeyScale = 256;        // move key = 2dF * 256 + colour
+constexpr int kMaxD2 = (1 << 23) - 1; // |2dF| bound so that the key fits int32
+
+// Philox counter purposes (third counter word = gen << 8 | purpose << 4 | phase)
+enum : uint32_t { kPurposeInit = 1, kPurposeTabu = 2, kPurposeXover = 3, kPurposeMatch = 4 };
+
+// Read-only device image of one reduced instance (Sec. 2.1-2.2, Alg. 1).
+struct DevInst {
+    int n;        // order
+    int n1p;      // row stride of the per-row / per-column colour count tables
+    int nv;       // |V|, reduced vertices in row-major cell order
+    int nw;       // ceil(nv / 32): words of a vertex bitmask or of a bit plane
+    int nb;       // bit planes needed for colours 0..n
+    const uint16_t *rc;      // [nv] row << 8 | column
+    const uint4 *dom;        // [nv] D(v) as a 128-bit mask, bit k = colour k
+    const uint8_t *ndom;     // [nv] |D(v)| (colour 0 included)
+    const int32_t *row_ptr;  // [n + 1] vertices of row r: row_v[row_ptr[r] .. row_ptr[r+1])
+    const uint16_t *row_v;   // [nv]
+    const int32_t *col_ptr;  // [n + 1]
+    const uint16_t *col_v;   // [nv]
+};
+
+// Scalar parameters of one local-search launch.
+struct LSArgs {
+    const uint8_t *S_in;
+    uint8_t *S_out;
+    int count, ind0, gen, flags;
+    int64_t iters1, iters2;       // phase-1 / PartialCol iterations, phase-2 iterations
+    uint32_t key0, key1;          // Philox key = seed
+    int phi2_1, phi2_2;           // 2*phi of phase 1 and phase 2
+    int alpha_num, alpha_den, tenure_rand;
+    int span1, span2;             // clock span reserved per phase (iterations + max tenure + 2)
+    int32_t *f_out;
+    int64_t *F_out;
+    plse_walk_stats *stats;
+    // scratch (global memory owned by the handle's workspace)
+    uint32_t *G;                  // [slots][nv * n1p] evicted tabu expiries (absolute clock)
+    uint32_t *slot_clock;         // [slots] next free clock value of each slot
+    int *work_counter;            // dynamic walk scheduler, zeroed before launch
+    int *error_flag;              // nonzero after a failed device bound check
+};
+
+struct LSLaunch {
+    int blocks;        // one warp per block; one walk slot per block
+    size_t smem;       // dynamic shared memory per block
+    int colour_words;  // 32-bit words of a colour mask actually used (1..4)
+};
+
+// Shared-memory plan of one walk slot (bytes).
+struct SmemPlan {
+    size_t off_S, off_R, off_K, off_cmask, off_clist, off_tc, total;
+};
+SmemPlan smem_plan(const DevInst &I);
+
+// Launchers (return cudaError_t of the launch; asynchronous).
+cudaError_t launch_init_population(const DevInst &I, int pop, uint64_t seed, uint8_t *P,
+                                   cudaStream_t st);
+cudaError_t launch_local_search(const DevInst &I, const LSArgs &a, const LSLaunch &L,
+                                cudaStream_t st);
+LSLaunch plan_local_search(const DevInst &I, int device, int count);
+
+}  // namespace plse

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libplse.so (the C ABI in include/plse.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (their ``data_ptr()`` is passed
+through); streams are torch streams (``torch.cuda.current_stream()`` by
+default).  If the library or a GPU is missing, calls raise ``PlseError``: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libplse.so")
+
+PLSE_OK, PLSE_EINVAL, PLSE_ENOMEM, PLSE_ECUDA = 0, -1, -2, -3
+PLSE_EBUSY, PLSE_ECANCELLED, PLSE_ENOTSUP, PLSE_ECHECK = -4, -5, -6, -7
+LS_PHASE1, LS_PHASE2, LS_REPAIR, LS_PARTIALCOL = 1, 2, 4, 8
+MODE_PLITS, MODE_PARTIALCOL = 0, 1
+MATCH_NEAREST, MATCH_RANDOM = 0, 1
+XOVER_AUX, XOVER_UX = 0, 1
+
+
+class PlseError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__("%s (%d)%s" % (_strerror(code), code, (": " + msg) if msg else ""))
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [(name, C.c_int32) for name in (
+        "alpha_num", "alpha_den", "tenure_rand", "phase1_phi2", "phase2_phi2_per_v",
+        "phase2_iter_per_v", "spacing_gamma", "beta", "mode", "matching", "crossover",
+        "tested_cap")]
+
+
+class WalkStats(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in (
+        "iterations", "moves", "cand", "pairs", "deg", "improvements", "uncolored")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+WALK_STATS_FIELDS = [k for k, _ in WalkStats._fields_]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("generations", C.c_int32), ("best_f", C.c_int32), ("walks", WalkStats),
+                ("ms_total", C.c_double), ("ms_local_search", C.c_double)]
+
+
+_lib = None
+
+# exported C symbols and their (restype, argtypes)
+_vp, _i32, _i64, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+SIGNATURES = {
+    "plse_create": (C.c_int, [C.c_int, _vp, C.POINTER(_vp)]),
+    "plse_destroy": (None, [_vp]),
+    "plse_strerror": (C.c_char_p, [C.c_int]),
+    "plse_last_error_detail": (C.c_int, [_vp, C.c_char_p, C.c_size_t]),
+    "plse_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "plse_sync": (C.c_int, [_vp, _vp]),
+    "plse_default_params": (None, [C.POINTER(Params)]),
+    "plse_set_params": (C.c_int, [_vp, C.POINTER(Params)]),
+    "plse_get_params": (C.c_int, [_vp, C.POINTER(Params)]),
+    "plse_solve": (C.c_int, [_vp, C.c_int, C.c_int, _i64, _u64, _vp, C.POINTER(C.c_int)]),
+    "plse_solve_ex": (C.c_int, [_vp, C.c_int, C.c_int, _i64, _u64, _vp, _vp, C.POINTER(C.c_int),
+                                C.POINTER(SolveStats)]),
+    "plse_init_population": (C.c_int, [_vp, C.c_int, _u64, _vp, _vp]),
+    "plse_local_search": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _i64, _u64, C.c_int,
+                                    _vp, _vp, _vp, _vp]),
+    "plse_distances": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp]),
+    "plse_pop_update": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "plse_matching": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, _u64, _vp, _vp, _vp]),
+    "plse_crossover": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, _u64, _vp, _vp]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Opens libplse.so (built by ``paper_2103_10453_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise PlseError(PLSE_ENOTSUP, "libplse.so not built (run __graft_entry__.build())")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _strerror(code):
+    try:
+        return load().plse_strerror(code).decode()
+    except Exception:
+        return "error"
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load().plse_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, int(v))
+    return p
+
+
+def _dptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise PlseError(PLSE_EINVAL, "expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise PlseError(PLSE_EINVAL, "expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Instance:
+    """A PLSE instance on the GPU (``plse_create``)."""
+
+    def __init__(self, grid):
+        grid = np.ascontiguousarray(grid, dtype=np.int8)
+        if grid.ndim != 2 or grid.shape[0] != grid.shape[1]:
+            raise PlseError(PLSE_EINVAL, "grid must be square")
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.plse_create(grid.shape[0], grid.ctypes.data, C.byref(h))
+        if rc != PLSE_OK:
+            raise PlseError(rc, "plse_create")
+        self.h = h
+        nv, l, ub = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.plse_info(self.h, C.byref(nv), C.byref(l), C.byref(ub)))
+        self.n, self.nv, self.l, self.ub = grid.shape[0], nv.value, l.value, ub.value
+        self.grid = grid.copy()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.plse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != PLSE_OK:
+            buf = C.create_string_buffer(512)
+            if getattr(self, "h", None):
+                self.lib.plse_last_error_detail(self.h, buf, 512)
+            raise PlseError(rc, buf.value.decode())
+
+    # ---- parameters ------------------------------------------------------
+    def set_params(self, params: Params):
+        self._check(self.lib.plse_set_params(self.h, C.byref(params)))
+
+    def get_params(self) -> Params:
+        p = Params()
+        self._check(self.lib.plse_get_params(self.h, C.byref(p)))
+        return p
+
+    def sync(self, stream=None):
+        self._check(self.lib.plse_sync(self.h, _stream(stream)))
+
+    # ---- whole solve -----------------------------------------------------
+    def solve(self, pop, generations, iters, seed, stream=None, with_stats=False):
+        grid = np.zeros((self.n, self.n), dtype=np.int8)
+        score = C.c_int()
+        st = SolveStats()
+        self._check(self.lib.plse_solve_ex(self.h, pop, generations, int(iters), seed,
+                                           _stream(stream), grid.ctypes.data, C.byref(score),
+                                           C.byref(st)))
+        out = {"best_grid": grid, "score": int(score.value)}
+        if with_stats:
+            out.update(generations=int(st.generations), best_f=int(st.best_f),
+                       walks=st.walks.as_dict(), ms_total=float(st.ms_total),
+                       ms_local_search=float(st.ms_local_search))
+        return out
+
+    # ---- steps (device tensors) ------------------------------------------
+    def init_population(self, pop, seed, out, stream=None):
+        self._check(self.lib.plse_init_population(self.h, pop, seed, _dptr(out), _stream(stream)))
+        return out
+
+    def local_search(self, S_in, S_out, count, ind0, gen, iters, seed, flags,
+                     f_out=None, F_out=None, stats=None, stream=None):
+        self._check(self.lib.plse_local_search(
+            self.h, _dptr(S_in), _dptr(S_out), count, ind0, gen, int(iters), seed, flags,
+            _dptr(f_out), _dptr(F_out), _dptr(stats), _stream(stream)))
+
+    def distances(self, A, na, B, nb, D, stream=None):
+        self._check(self.lib.plse_distances(self.h, _dptr(A), na, _dptr(B), nb, _dptr(D),
+                                            _stream(stream)))
+
+    def pop_update(self, p, Pall, e, sel, filled=None, stream=None):
+        self._check(self.lib.plse_pop_update(self.h, p, _dptr(Pall), _dptr(e), _dptr(sel),
+                                             _dptr(filled), _stream(stream)))
+
+    def matching(self, p, P, uid, tested, tcount, gen, seed, partner, dist, stream=None):
+        self._check(self.lib.plse_matching(self.h, p, _dptr(P), _dptr(uid), _dptr(tested),
+                                           _dptr(tcount), gen, seed, _dptr(partner), _dptr(dist),
+                                           _stream(stream)))
+
+    def crossover(self, p, P, partner, dist, gen, seed, O, stream=None):
+        self._check(self.lib.plse_crossover(self.h, p, _dptr(P), _dptr(partner), _dptr(dist),
+                                            gen, seed, _dptr(O), _stream(stream)))
