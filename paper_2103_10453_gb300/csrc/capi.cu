@@ -52,6 +52,15 @@ int build_instance(plse_instance *h, int n, const int8_t *grid)
             rowm[r].set(k);
             colm[c].set(k);
         }
+    // colours still allowed by each row and each column
+    h->allow_row.assign(n, make_uint4(0, 0, 0, 0));
+    h->allow_col.assign(n, make_uint4(0, 0, 0, 0));
+    for (int r = 0; r < n; ++r)
+        for (int k = 1; k <= n; ++k) {
+            uint32_t *ar = &h->allow_row[r].x, *ac = &h->allow_col[r].x;
+            if (!rowm[r].has(k)) ar[k >> 5] |= 1u << (k & 31);
+            if (!colm[r].has(k)) ac[k >> 5] |= 1u << (k & 31);
+        }
     // D(v) = {0} u ({1..n} minus the row's and column's symbols); empty cells
     // with D(v) = {0} are removed and counted in l (Alg. 1).
     h->cell.clear();
@@ -112,6 +121,8 @@ int upload_instance(plse_instance *h)
     const size_t o_rv = off; off = up256(off + 2 * (size_t)nv + 2);
     const size_t o_cp = off; off = up256(off + 4 * (size_t)(n + 1));
     const size_t o_cv = off; off = up256(off + 2 * (size_t)nv + 2);
+    const size_t o_ar = off; off = up256(off + 16 * (size_t)n);
+    const size_t o_ac = off; off = up256(off + 16 * (size_t)n);
     cudaError_t e = cudaMalloc(&h->inst_mem, off);
     if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "instance upload: %s", cudaGetErrorString(e));
     std::vector<uint8_t> img(off, 0);
@@ -122,6 +133,8 @@ int upload_instance(plse_instance *h)
         memcpy(img.data() + o_rv, h->row_v.data(), 2 * (size_t)nv);
         memcpy(img.data() + o_cv, h->col_v.data(), 2 * (size_t)nv);
     }
+    memcpy(img.data() + o_ar, h->allow_row.data(), 16 * (size_t)n);
+    memcpy(img.data() + o_ac, h->allow_col.data(), 16 * (size_t)n);
     memcpy(img.data() + o_rp, h->row_ptr.data(), 4 * (size_t)(n + 1));
     memcpy(img.data() + o_cp, h->col_ptr.data(), 4 * (size_t)(n + 1));
     e = cudaMemcpy(h->inst_mem, img.data(), off, cudaMemcpyHostToDevice);
@@ -142,6 +155,8 @@ int upload_instance(plse_instance *h)
     I.row_v = reinterpret_cast<const uint16_t *>(b + o_rv);
     I.col_ptr = reinterpret_cast<const int32_t *>(b + o_cp);
     I.col_v = reinterpret_cast<const uint16_t *>(b + o_cv);
+    I.allow_row = reinterpret_cast<const uint4 *>(b + o_ar);
+    I.allow_col = reinterpret_cast<const uint4 *>(b + o_ac);
     return PLSE_OK;
 }
 
@@ -207,7 +222,7 @@ int ensure_ls_workspace(plse_instance *h, int slots)
 
 int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
                          int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
-                         int64_t *F_out, plse_walk_stats *stats, cudaStream_t st)
+                         int64_t *F_out, plse_walk_stats *stats, cudaStream_t st, const int *skip)
 {
     const plse_params &p = h->params;
     LSArgs a;
@@ -232,7 +247,8 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.f_out = f_out;
     a.F_out = F_out;
     a.stats = stats;
-    LSLaunch L = plan_local_search(h->di, h->device, count);
+    a.skip = skip;
+    LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_warps > 0 ? h->ls_warps : default_ls_warps(h->di));
     if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "local search does not fit on this device");
     int rc = ensure_ls_workspace(h, L.blocks);
     if (rc) return rc;
@@ -347,6 +363,14 @@ int plse_get_params(plse_handle h, plse_params *p)
 {
     if (!h || !p) return PLSE_EINVAL;
     *p = h->params;
+    return PLSE_OK;
+}
+
+int plse_set_launch(plse_handle h, int ls_warps)
+{
+    if (!h || !(ls_warps == 0 || ls_warps == 1 || ls_warps == 2 || ls_warps == 4 || ls_warps == 8))
+        return PLSE_EINVAL;
+    h->ls_warps = ls_warps;
     return PLSE_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "plse_internal.cuh"
+#include "plse_pop.cuh"
 
 namespace plse {
 
@@ -33,11 +34,16 @@ struct plse_instance {
     std::vector<uint8_t> ndom;
     std::vector<int32_t> row_ptr, col_ptr;
     std::vector<uint16_t> row_v, col_v;
+    std::vector<uint4> allow_row, allow_col;
+    int ls_warps = 0;                  // warps per walk of the local search (0 = automatic)
     plse_params params{};
     void *inst_mem = nullptr;        // one device allocation holding the DevInst arrays
     plse::DevInst di{};
     plse::Workspace ws;
     plse::SolverState *solver = nullptr;
+    uint32_t *step_planes = nullptr;   // bit planes for the population step entry points
+    size_t step_planes_cap = 0;
+    plse::PopScratch step_ps;          // Alg. 4 scratch for plse_pop_update
     std::string err;
 };
 
@@ -47,6 +53,7 @@ int cuda_fail(plse_instance *h, cudaError_t e, const char *where);
 int max_tenure(const plse_instance *h);
 int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
                          int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
-                         int64_t *F_out, plse_walk_stats *stats, cudaStream_t st);
+                         int64_t *F_out, plse_walk_stats *stats, cudaStream_t st,
+                         const int *skip = nullptr);
 void release_solver(plse_instance *h);
 }  // namespace plse

@@ -34,6 +34,9 @@ struct DevInst {
     const uint16_t *row_v;   // [nv]
     const int32_t *col_ptr;  // [n + 1]
     const uint16_t *col_v;   // [nv]
+    const uint4 *allow_row;  // [n] colours 1..n not prefilled in row r (bit k = colour k)
+    const uint4 *allow_col;  // [n] colours 1..n not prefilled in column c
+    // D(v) \ {0} = allow_row[row(v)] & allow_col[col(v)] for every reduced vertex
 };
 
 // Scalar parameters of one local-search launch.
@@ -54,17 +57,20 @@ struct LSArgs {
     uint32_t *slot_clock;         // [slots] next free clock value of each slot
     int *work_counter;            // dynamic walk scheduler, zeroed before launch
     int *error_flag;              // nonzero after a failed device bound check
+    const int *skip;              // if non-null and nonzero at launch: return at once
 };
 
 struct LSLaunch {
-    int blocks;        // one warp per block; one walk slot per block
+    int blocks;        // one walk slot per block (persistent over walks)
+    int warps;         // warps per block working on one walk (1, 2, 4 or 8)
     size_t smem;       // dynamic shared memory per block
     int colour_words;  // 32-bit words of a colour mask actually used (1..4)
 };
 
 // Shared-memory plan of one walk slot (bytes).
 struct SmemPlan {
-    size_t off_S, off_R, off_K, off_cmask, off_clist, off_tc, total;
+    size_t off_rc, off_allow, off_S, off_B, off_R, off_K, off_RP, off_KP, off_cmask, off_clist,
+        off_tc, off_red, total;
 };
 SmemPlan smem_plan(const DevInst &I);
 
@@ -73,6 +79,7 @@ cudaError_t launch_init_population(const DevInst &I, int pop, uint64_t seed, uin
                                    cudaStream_t st);
 cudaError_t launch_local_search(const DevInst &I, const LSArgs &a, const LSLaunch &L,
                                 cudaStream_t st);
-LSLaunch plan_local_search(const DevInst &I, int device, int count);
+LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps);
+int default_ls_warps(const DevInst &I);
 
 }  // namespace plse

@@ -1,0 +1,43 @@
+// plse_pop.cuh -- population-level kernels (k_population.cu), library-internal.
+#pragma once
+
+#include "plse_internal.cuh"
+
+namespace plse {
+
+constexpr int kChunk = 128;   // Alg. 4 candidates resolved per sequential step
+
+// device-side progress of one Alg. 4 pass
+struct SelState {
+    int nacc;             // members accepted so far
+    int nrej;             // candidates rejected so far (in rank order)
+    int done;             // nacc reached p
+    int chunk_acc_start;  // nacc when the current chunk started
+};
+
+// device scratch of Alg. 4 for populations of up to `cap_p`
+struct PopScratch {
+    int cap_p = 0;
+    int32_t *order = nullptr;  // [2p] candidates in (e, index) order
+    int32_t *mind = nullptr;   // [2p] min distance to the accepted set, by rank
+    int32_t *acc = nullptr;    // [p] accepted candidates in acceptance order
+    int32_t *rej = nullptr;    // [2p] rejected candidates in rank order
+    uint16_t *Dloc = nullptr;  // [chunks][kChunk][kChunk] chunk-local distances
+    SelState *sel_state = nullptr;
+};
+
+cudaError_t launch_planes(const DevInst &I, const uint8_t *P, int count, uint32_t *planes, cudaStream_t st);
+cudaError_t launch_distance_matrix(const DevInst &I, const uint32_t *planesA, int na,
+                                   const uint32_t *planesB, int nb, int32_t *D, cudaStream_t st);
+cudaError_t launch_pop_update(const DevInst &I, int p, const uint32_t *planes, const int64_t *e,
+                              int gamma, const PopScratch &ps, int32_t *sel, int32_t *filled,
+                              const int *skip, cudaStream_t st);
+cudaError_t launch_matching(const DevInst &I, int p, const uint32_t *planes, const uint32_t *uid,
+                            uint32_t *tested, int32_t *tcount, int cap, int random, int gen,
+                            uint64_t seed, int32_t *partner, int32_t *dist, const int *skip,
+                            cudaStream_t st);
+cudaError_t launch_crossover(const DevInst &I, int p, const uint8_t *P, const int32_t *partner,
+                             const int32_t *dist, int gen, uint64_t seed, int beta, int ux, uint8_t *O,
+                             const int *skip, cudaStream_t st);
+
+}  // namespace plse

@@ -1,11 +1,485 @@
-// solve.cu -- placeholder, replaced by the generation-loop driver.
+// solve.cu -- the generation loop of MPMA (Alg. 2) on one GPU, its bookkeeping
+// kernels (initial evaluation, best-solution update, population gather) and the
+// population-level step entry points of the C ABI.
+//
+// Per generation, all on one stream and all on the device:
+//   local search of the offspring S^O -> P'          (Alg. 3 twice + repair)
+//   best update S* / f*, optimality flag              (Alg. 2)
+//   bit planes of P', Alg. 4 over P_t u P' -> P_{t+1} (distances on the fly)
+//   gather P_{t+1} (colourings, planes, scores, uids, tested lists)
+//   matching + AUX -> next S^O                        (Alg. 5)
+// Once the bound is reached every later kernel of the run returns at entry, so
+// the host only reads the 4-byte flag once per generation.
+#include <climits>
+#include <cstring>
+
 #include "plse_handle.cuh"
-namespace plse { void release_solver(plse_instance *) {} }
-extern "C" {
-int plse_solve(plse_handle h, int, int, int64_t, uint64_t, int8_t *, int *) { return h ? PLSE_ENOTSUP : PLSE_EINVAL; }
-int plse_solve_ex(plse_handle h, int, int, int64_t, uint64_t, void *, int8_t *, int *, plse_solve_stats *) { return h ? PLSE_ENOTSUP : PLSE_EINVAL; }
-int plse_distances(plse_handle h, const uint8_t *, int, const uint8_t *, int, int32_t *, void *) { return h ? PLSE_ENOTSUP : PLSE_EINVAL; }
-int plse_pop_update(plse_handle h, int, const uint8_t *, const int64_t *, int32_t *, int32_t *, void *) { return h ? PLSE_ENOTSUP : PLSE_EINVAL; }
-int plse_matching(plse_handle h, int, const uint8_t *, const uint32_t *, uint32_t *, int32_t *, int, uint64_t, int32_t *, int32_t *, void *) { return h ? PLSE_ENOTSUP : PLSE_EINVAL; }
-int plse_crossover(plse_handle h, int, const uint8_t *, const int32_t *, const int32_t *, int, uint64_t, uint8_t *, void *) { return h ? PLSE_ENOTSUP : PLSE_EINVAL; }
+#include "plse_pop.cuh"
+
+namespace plse {
+
+struct Ctrl {
+    int fstar;      // f(S*)
+    int done;       // bound reached: later kernels return at entry
+    int gens;       // generations executed
+    int pad;
+    long long stats[7];   // summed plse_walk_stats of every walk
+};
+
+struct SolverState {
+    int cap_p = 0, cap_gens = 0;
+    uint8_t *Pall[2] = {nullptr, nullptr};   // [2p][nv]: P_t then P'
+    uint32_t *planes[2] = {nullptr, nullptr};// [2p][nw*nb]
+    int64_t *e[2] = {nullptr, nullptr};      // [2p]
+    uint32_t *uid[2] = {nullptr, nullptr};   // [p]
+    uint32_t *tested[2] = {nullptr, nullptr};// [p][cap]
+    int32_t *tcount[2] = {nullptr, nullptr}; // [p]
+    int tested_cap = 0;
+    uint8_t *SO = nullptr;                   // [p][nv] offspring
+    int32_t *fprime = nullptr, *sel = nullptr, *partner = nullptr, *dist = nullptr;
+    plse_walk_stats *wstats = nullptr;
+    PopScratch ps;
+    Ctrl *ctrl = nullptr;
+    uint8_t *Sstar = nullptr;
+    int32_t *trace = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// f and c of each colouring (Eq. 1, 3), ranking score e = f + |V| c (one warp each)
+__global__ void __launch_bounds__(32) eval_kernel(const DevInst I, const uint8_t *P, int count, int64_t *e)
+{
+    extern __shared__ __align__(16) uint8_t cnt[];   // R then K, n x n1p each
+    const int lane = threadIdx.x;
+    for (int x = blockIdx.x; x < count; x += gridDim.x) {
+        const uint8_t *S = P + (size_t)x * I.nv;
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(cnt);
+        for (int q = lane; q < (2 * I.n * I.n1p) / 4; q += 32) w32[q] = 0u;
+        __syncwarp();
+        for (int r = lane; r < I.n; r += 32) {
+            for (int q = I.row_ptr[r]; q < I.row_ptr[r + 1]; ++q) {
+                const int k = S[I.row_v[q]];
+                if (k) cnt[r * I.n1p + k] += 1;
+            }
+            for (int q = I.col_ptr[r]; q < I.col_ptr[r + 1]; ++q) {
+                const int k = S[I.col_v[q]];
+                if (k) cnt[I.n * I.n1p + r * I.n1p + k] += 1;
+            }
+        }
+        __syncwarp();
+        long long c = 0;
+        for (int q = lane; q < 2 * I.n * I.n1p; q += 32) c += cnt[q] * (cnt[q] - 1) / 2;
+        int f = 0;
+        for (int v = lane; v < I.nv; v += 32) f += S[v] == 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(FULL, c, o);
+            f += __shfl_xor_sync(FULL, f, o);
+        }
+        if (lane == 0) e[x] = (int64_t)f + (int64_t)I.nv * c;
+        __syncwarp();
+    }
 }
+
+// Alg. 2: S'* = argmin f over the (legal) offspring, S* replaced if strictly better
+__global__ void __launch_bounds__(1024) best_kernel(int p, int nv, int ftarget, int gen,
+                                                    const int32_t *fprime, const uint8_t *Pp,
+                                                    const plse_walk_stats *ws, int64_t *e_p,
+                                                    Ctrl *ctrl, uint8_t *Sstar, int32_t *trace)
+{
+    if (ctrl->done) return;
+    __shared__ uint32_t skey[32];
+    __shared__ long long sst[7][32];
+    uint32_t key = 0xffffffffu;
+    long long st[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        const int f = fprime[i];
+        e_p[i] = f;                       // legal after repair / PartialCol: e = f
+        key = min(key, ((uint32_t)f << 16) | (uint32_t)i);
+        const long long *s = reinterpret_cast<const long long *>(ws + i);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) st[k] += s[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        key = min(key, __shfl_xor_sync(FULL, key, o));
+#pragma unroll
+        for (int k = 0; k < 7; ++k) st[k] += __shfl_xor_sync(FULL, st[k], o);
+    }
+    if (lane == 0) {
+        skey[wid] = key;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) sst[k][wid] = st[k];
+    }
+    __syncthreads();
+    __shared__ int s_best, s_take;
+    if (threadIdx.x == 0) {
+        uint32_t kmin = 0xffffffffu;
+        const int nw = (blockDim.x + 31) / 32;
+        for (int q = 0; q < nw; ++q) kmin = min(kmin, skey[q]);
+        for (int k = 0; k < 7; ++k) {
+            long long t = 0;
+            for (int q = 0; q < nw; ++q) t += sst[k][q];
+            ctrl->stats[k] += t;
+        }
+        const int fb = (int)(kmin >> 16);
+        s_best = (int)(kmin & 0xffffu);
+        s_take = fb < ctrl->fstar;
+        if (s_take) ctrl->fstar = fb;
+        trace[gen] = ctrl->fstar;
+        ctrl->gens = gen + 1;
+        if (ctrl->fstar <= ftarget) ctrl->done = 1;
+    }
+    __syncthreads();
+    if (s_take)
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) Sstar[v] = Pp[(size_t)s_best * nv + v];
+}
+
+// P_{t+1}[q] = P_all[sel[q]] with its planes, score, uid and tested list (warp per q)
+__global__ void gather_kernel(const DevInst I, int p, int gen, const int32_t *sel,
+                              const uint8_t *Pall, const uint32_t *planes, const int64_t *e,
+                              const uint32_t *uid, const uint32_t *tested, const int32_t *tcount,
+                              int cap, uint8_t *Pn, uint32_t *planesn, int64_t *en, uint32_t *uidn,
+                              uint32_t *testedn, int32_t *tcountn, const int *skip)
+{
+    if (*skip) return;
+    const int lane = threadIdx.x & 31;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= p) return;
+    const int s = sel[q];
+    const uint8_t *src = Pall + (size_t)s * I.nv;
+    uint8_t *dst = Pn + (size_t)q * I.nv;
+    for (int v = lane; v < I.nv; v += 32) dst[v] = src[v];
+    const size_t stride = (size_t)I.nw * I.nb;
+    for (size_t k = lane; k < stride; k += 32) planesn[(size_t)q * stride + k] = planes[(size_t)s * stride + k];
+    if (s < p) {
+        const int c = tcount[s];
+        for (int k = lane; k < c; k += 32) testedn[(size_t)q * cap + k] = tested[(size_t)s * cap + k];
+        if (lane == 0) { tcountn[q] = c; uidn[q] = uid[s]; }
+    } else if (lane == 0) {
+        tcountn[q] = 0;
+        uidn[q] = ((uint32_t)(gen + 1) << 16) | (uint32_t)(s - p);   // uid of a new member
+    }
+    if (lane == 0) en[q] = e[s];
+}
+
+__global__ void init_ids_kernel(int p, uint32_t *uid, int32_t *tcount)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p) { uid[i] = (uint32_t)i; tcount[i] = 0; }
+}
+
+__global__ void init_ctrl_kernel(Ctrl *ctrl, int nv, int ftarget)
+{
+    ctrl->fstar = nv;
+    ctrl->done = nv <= ftarget;
+    ctrl->gens = 0;
+    for (int k = 0; k < 7; ++k) ctrl->stats[k] = 0;
+}
+
+template <typename T>
+int dalloc(plse_instance *h, T *&p, size_t n)
+{
+    if (p) { cudaFree(p); p = nullptr; }
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) { p = nullptr; return fail(h, PLSE_ENOMEM, "solver allocation: %s", cudaGetErrorString(e)); }
+    return PLSE_OK;
+}
+
+}  // namespace
+
+int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p)
+{
+    if (p <= ps.cap_p) return PLSE_OK;
+    const int m = 2 * p, nchunks = (m + kChunk - 1) / kChunk;
+    int rc;
+    if ((rc = dalloc(h, ps.order, m)) || (rc = dalloc(h, ps.mind, m)) || (rc = dalloc(h, ps.acc, p)) ||
+        (rc = dalloc(h, ps.rej, m)) || (rc = dalloc(h, ps.Dloc, (size_t)nchunks * kChunk * kChunk)) ||
+        (rc = dalloc(h, ps.sel_state, 1)))
+        return rc;
+    ps.cap_p = p;
+    return PLSE_OK;
+}
+
+void free_pop_scratch(PopScratch &ps)
+{
+    cudaFree(ps.order); cudaFree(ps.mind); cudaFree(ps.acc); cudaFree(ps.rej);
+    cudaFree(ps.Dloc); cudaFree(ps.sel_state);
+    ps = PopScratch();
+}
+
+void release_solver(plse_instance *h)
+{
+    SolverState *s = h->solver;
+    if (!s) return;
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(s->Pall[k]); cudaFree(s->planes[k]); cudaFree(s->e[k]);
+        cudaFree(s->uid[k]); cudaFree(s->tested[k]); cudaFree(s->tcount[k]);
+    }
+    cudaFree(s->SO); cudaFree(s->fprime); cudaFree(s->sel); cudaFree(s->partner); cudaFree(s->dist);
+    cudaFree(s->wstats); cudaFree(s->ctrl); cudaFree(s->Sstar); cudaFree(s->trace);
+    free_pop_scratch(s->ps);
+    for (auto &ev : s->ev) if (ev) cudaEventDestroy(ev);
+    delete s;
+    h->solver = nullptr;
+    // step scratch
+    cudaFree(h->step_planes);
+    h->step_planes = nullptr;
+    h->step_planes_cap = 0;
+    free_pop_scratch(h->step_ps);
+}
+
+static int ensure_solver(plse_instance *h, int p, int gens)
+{
+    SolverState *s = h->solver;
+    const int cap = h->params.tested_cap;
+    if (s && s->cap_p >= p && s->cap_gens >= gens && s->tested_cap == cap) return PLSE_OK;
+    if (s) {
+        // keep the step scratch, rebuild the solver buffers
+        SolverState *old = s;
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(old->Pall[k]); cudaFree(old->planes[k]); cudaFree(old->e[k]);
+            cudaFree(old->uid[k]); cudaFree(old->tested[k]); cudaFree(old->tcount[k]);
+        }
+        cudaFree(old->SO); cudaFree(old->fprime); cudaFree(old->sel); cudaFree(old->partner);
+        cudaFree(old->dist); cudaFree(old->wstats); cudaFree(old->ctrl); cudaFree(old->Sstar);
+        cudaFree(old->trace);
+        free_pop_scratch(old->ps);
+        for (auto &ev : old->ev) if (ev) cudaEventDestroy(ev);
+        delete old;
+        h->solver = nullptr;
+    }
+    s = new SolverState();
+    h->solver = s;
+    const DevInst &I = h->di;
+    const size_t PV = (size_t)p * I.nv, stride = (size_t)I.nw * I.nb;
+    int rc;
+    for (int k = 0; k < 2; ++k) {
+        if ((rc = dalloc(h, s->Pall[k], 2 * PV)) || (rc = dalloc(h, s->planes[k], 2 * (size_t)p * stride)) ||
+            (rc = dalloc(h, s->e[k], 2 * (size_t)p)) || (rc = dalloc(h, s->uid[k], (size_t)p)) ||
+            (rc = dalloc(h, s->tested[k], (size_t)p * cap)) || (rc = dalloc(h, s->tcount[k], (size_t)p)))
+            return rc;
+    }
+    if ((rc = dalloc(h, s->SO, PV)) || (rc = dalloc(h, s->fprime, (size_t)p)) || (rc = dalloc(h, s->sel, (size_t)p)) ||
+        (rc = dalloc(h, s->partner, (size_t)p)) || (rc = dalloc(h, s->dist, (size_t)p)) ||
+        (rc = dalloc(h, s->wstats, (size_t)p)) || (rc = dalloc(h, s->ctrl, 1)) ||
+        (rc = dalloc(h, s->Sstar, (size_t)I.nv)) || (rc = dalloc(h, s->trace, (size_t)gens)))
+        return rc;
+    if ((rc = ensure_pop_scratch(h, s->ps, p))) return rc;
+    for (auto &ev : s->ev)
+        if (cudaEventCreate(&ev) != cudaSuccess) return fail(h, PLSE_ECUDA, "event create");
+    s->cap_p = p;
+    s->cap_gens = gens;
+    s->tested_cap = cap;
+    return PLSE_OK;
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);       \
+    } while (0)
+
+int run_solve(plse_instance *h, int pop, int generations, int64_t iters, uint64_t seed, cudaStream_t st,
+              int8_t *best_grid, int *best_score, plse_solve_stats *stats, int32_t *trace_out)
+{
+    if (pop < 2 || pop > 65535 || generations < 0 || generations > 65534 || iters < 0 || iters > (1ll << 30))
+        return fail(h, PLSE_EINVAL, "plse_solve: invalid argument");
+    const DevInst &I = h->di;
+    const plse_params &prm = h->params;
+    const int nv = h->nv;
+    const int ftarget = h->l == 1 ? 1 : 0;
+    int fstar = nv, gens_done = 0;
+    std::vector<uint8_t> Sstar_h((size_t)nv, 0);
+    double ms_total = 0, ms_ls = 0;
+    long long wst[7] = {0, 0, 0, 0, 0, 0, 0};
+
+    if (nv > 0 && fstar > ftarget && generations > 0) {
+        int rc = ensure_solver(h, pop, generations);
+        if (rc) return rc;
+        SolverState *s = h->solver;
+        const int p = pop, cap = prm.tested_cap;
+        const size_t PV = (size_t)p * nv, stride = (size_t)I.nw * I.nb;
+        CK(cudaEventRecord(s->ev[0], st));
+        // P_0, its scores, planes, ids; S^O = P_0; S* = empty colouring, f* = |V|
+        CK(launch_init_population(I, p, seed, s->Pall[0], st));
+        const size_t cnt_smem = 2 * (size_t)I.n * I.n1p;
+        eval_kernel<<<std::min(p, 65535), 32, cnt_smem, st>>>(I, s->Pall[0], p, s->e[0]);
+        CK(cudaGetLastError());
+        CK(launch_planes(I, s->Pall[0], p, s->planes[0], st));
+        init_ids_kernel<<<(p + 255) / 256, 256, 0, st>>>(p, s->uid[0], s->tcount[0]);
+        init_ctrl_kernel<<<1, 1, 0, st>>>(s->ctrl, nv, ftarget);
+        CK(cudaMemsetAsync(s->Sstar, 0, (size_t)nv, st));
+        CK(cudaMemcpyAsync(s->SO, s->Pall[0], PV, cudaMemcpyDeviceToDevice, st));
+        CK(cudaGetLastError());
+        const int *skip = &s->ctrl->done;
+        const int flags = prm.mode == PLSE_MODE_PARTIALCOL ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
+                                                           : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
+        int cur = 0;
+        for (int g = 0; g < generations; ++g) {
+            const int nxt = cur ^ 1;
+            uint8_t *Pp = s->Pall[cur] + PV;
+            CK(cudaEventRecord(s->ev[1], st));
+            rc = enqueue_local_search(h, s->SO, Pp, p, 0, g, iters, seed, flags, s->fprime, nullptr,
+                                      s->wstats, st, skip);
+            if (rc) return rc;
+            CK(cudaEventRecord(s->ev[2], st));
+            best_kernel<<<1, 1024, 0, st>>>(p, nv, ftarget, g, s->fprime, Pp, s->wstats, s->e[cur] + p,
+                                            s->ctrl, s->Sstar, s->trace);
+            CK(cudaGetLastError());
+            // the stop test needs f* on the host: one 8-byte read per generation
+            int hc[2];
+            CK(cudaMemcpyAsync(hc, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, s->ev[1], s->ev[2]));
+            ms_ls += ms;
+            gens_done = g + 1;
+            if (hc[1]) break;
+            CK(launch_planes(I, Pp, p, s->planes[cur] + (size_t)p * stride, st));
+            CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel,
+                                 nullptr, skip, st));
+            gather_kernel<<<(p * 32 + 255) / 256, 256, 0, st>>>(
+                I, p, g, s->sel, s->Pall[cur], s->planes[cur], s->e[cur], s->uid[cur], s->tested[cur],
+                s->tcount[cur], cap, s->Pall[nxt], s->planes[nxt], s->e[nxt], s->uid[nxt],
+                s->tested[nxt], s->tcount[nxt], skip);
+            CK(cudaGetLastError());
+            CK(launch_matching(I, p, s->planes[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], cap,
+                               prm.matching == PLSE_MATCH_RANDOM, g, seed, s->partner, s->dist, skip, st));
+            CK(launch_crossover(I, p, s->Pall[nxt], s->partner, s->dist, g, seed, prm.beta,
+                                prm.crossover == PLSE_XOVER_UX, s->SO, skip, st));
+            cur = nxt;
+        }
+        CK(cudaEventRecord(s->ev[3], st));
+        Ctrl hctrl;
+        CK(cudaMemcpyAsync(&hctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(Sstar_h.data(), s->Sstar, (size_t)nv, cudaMemcpyDeviceToHost, st));
+        if (trace_out) CK(cudaMemcpyAsync(trace_out, s->trace, sizeof(int32_t) * gens_done, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        float mt = 0;
+        CK(cudaEventElapsedTime(&mt, s->ev[0], s->ev[3]));
+        ms_total = mt;
+        fstar = hctrl.fstar;
+        gens_done = hctrl.gens;
+        for (int k = 0; k < 7; ++k) wst[k] = hctrl.stats[k];
+        // device-side consistency checks of the local search
+        int flag = 0;
+        CK(cudaMemcpy(&flag, h->ws.counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            cudaMemset(h->ws.counters + 1, 0, sizeof(int));
+            return fail(h, PLSE_ECHECK, "a local-search consistency check failed");
+        }
+    }
+    const int n = h->n;
+    if (best_grid) {
+        memcpy(best_grid, h->grid.data(), (size_t)n * n);
+        for (int v = 0; v < nv; ++v) best_grid[h->cell[v]] = (int8_t)Sstar_h[v];
+    }
+    if (best_score) *best_score = n * n - h->l - fstar;
+    if (stats) {
+        stats->generations = gens_done;
+        stats->best_f = fstar;
+        int64_t *w = &stats->walks.iterations;
+        for (int k = 0; k < 7; ++k) w[k] = wst[k];
+        stats->ms_total = ms_total;
+        stats->ms_local_search = ms_ls;
+    }
+    return PLSE_OK;
+}
+
+int ensure_step_planes(plse_instance *h, size_t individuals)
+{
+    const size_t need = individuals * (size_t)h->di.nw * h->di.nb;
+    if (need <= h->step_planes_cap) return PLSE_OK;
+    int rc = dalloc(h, h->step_planes, need);
+    if (rc) return rc;
+    h->step_planes_cap = need;
+    return PLSE_OK;
+}
+
+}  // namespace plse
+
+using namespace plse;
+
+extern "C" {
+
+int plse_solve(plse_handle h, int pop, int generations, int64_t iters, uint64_t seed, int8_t *best_grid,
+               int *best_score)
+{
+    if (!h) return PLSE_EINVAL;
+    return run_solve(h, pop, generations, iters, seed, nullptr, best_grid, best_score, nullptr, nullptr);
+}
+
+int plse_solve_ex(plse_handle h, int pop, int generations, int64_t iters, uint64_t seed, void *stream,
+                  int8_t *best_grid, int *best_score, plse_solve_stats *stats)
+{
+    if (!h) return PLSE_EINVAL;
+    return run_solve(h, pop, generations, iters, seed, (cudaStream_t)stream, best_grid, best_score, stats,
+                     nullptr);
+}
+
+int plse_distances(plse_handle h, const uint8_t *A, int na, const uint8_t *B, int nb, int32_t *D, void *stream)
+{
+    if (!h || na < 0 || nb < 0) return PLSE_EINVAL;
+    if (na == 0 || nb == 0) return PLSE_OK;
+    if (!D || (h->nv > 0 && (!A || !B))) return fail(h, PLSE_EINVAL, "plse_distances: null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->nv == 0) {
+        CK(cudaMemsetAsync(D, 0, sizeof(int32_t) * (size_t)na * nb, st));
+        return PLSE_OK;
+    }
+    int rc = ensure_step_planes(h, (size_t)na + nb);
+    if (rc) return rc;
+    uint32_t *pa = h->step_planes, *pb = h->step_planes + (size_t)na * h->di.nw * h->di.nb;
+    CK(launch_planes(h->di, A, na, pa, st));
+    CK(launch_planes(h->di, B, nb, pb, st));
+    CK(launch_distance_matrix(h->di, pa, na, pb, nb, D, st));
+    return PLSE_OK;
+}
+
+int plse_pop_update(plse_handle h, int p, const uint8_t *Pall, const int64_t *e, int32_t *sel, int32_t *filled,
+                    void *stream)
+{
+    if (!h || p < 1 || p > 65535 || !e || !sel || (h->nv > 0 && !Pall))
+        return PLSE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_step_planes(h, 2 * (size_t)p);
+    if (rc) return rc;
+    if ((rc = ensure_pop_scratch(h, h->step_ps, p))) return rc;
+    if (h->nv > 0) CK(launch_planes(h->di, Pall, 2 * p, h->step_planes, st));
+    CK(launch_pop_update(h->di, p, h->step_planes, e, h->params.spacing_gamma, h->step_ps, sel, filled,
+                         nullptr, st));
+    return PLSE_OK;
+}
+
+int plse_matching(plse_handle h, int p, const uint8_t *P, const uint32_t *uid, uint32_t *tested,
+                  int32_t *tcount, int gen, uint64_t seed, int32_t *partner, int32_t *dist, void *stream)
+{
+    if (!h || p < 2 || p > 65535 || gen < 0 || gen >= (1 << 24) || !partner || !dist ||
+        (h->nv > 0 && !P) || (h->params.matching == PLSE_MATCH_NEAREST && (!uid || !tested || !tcount)))
+        return PLSE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_step_planes(h, (size_t)p);
+    if (rc) return rc;
+    if (h->nv > 0) CK(launch_planes(h->di, P, p, h->step_planes, st));
+    CK(launch_matching(h->di, p, h->step_planes, uid, tested, tcount, h->params.tested_cap,
+                       h->params.matching == PLSE_MATCH_RANDOM, gen, seed, partner, dist, nullptr, st));
+    return PLSE_OK;
+}
+
+int plse_crossover(plse_handle h, int p, const uint8_t *P, const int32_t *partner, const int32_t *dist, int gen,
+                   uint64_t seed, uint8_t *O, void *stream)
+{
+    if (!h || p < 1 || gen < 0 || gen >= (1 << 24) || !partner || !dist || (h->nv > 0 && (!P || !O)) || P == O)
+        return PLSE_EINVAL;
+    CK(launch_crossover(h->di, p, P, partner, dist, gen, seed, h->params.beta,
+                        h->params.crossover == PLSE_XOVER_UX, O, nullptr, (cudaStream_t)stream));
+    return PLSE_OK;
+}
+
+}  // extern "C"

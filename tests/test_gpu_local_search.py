@@ -170,3 +170,25 @@ def test_aliasing_and_uneven_params(plse, oracle_mod):
     for w in range(8):
         So, _, _ = oracle_ls(I, P[w], 100 + w, 7, 500, 3, 3, prm=oprm)
         assert np.array_equal(S[w], So)
+
+
+@pytest.mark.parametrize("warps", [1, 2, 4, 8])
+@pytest.mark.parametrize("name", ["ri_n16_r06", "cyc_n33_r03", "cyc_n70_r06", "ri_n100_r08"])
+def test_warps_per_walk_do_not_change_results(plse, oracle_mod, name, warps):
+    grid = cases()[name]
+    G, I = plse.Instance(grid), oracle_mod.Instance(grid)
+    G.set_launch(warps)
+    count = 12
+    iters = min(2 * I.nv, 2500)
+    P = I.init_population(count, 13)
+    flags = plse.LS_PHASE1 | plse.LS_PHASE2 | plse.LS_REPAIR
+    S, f, F, st = run_gpu_ls(plse, G, P, 5, 9, iters, 31, flags)
+    for w in range(count):
+        So, Fo, sto = oracle_ls(I, P[w], 5 + w, 9, iters, 31, flags)
+        assert np.array_equal(S[w], So), (name, warps, w)
+        assert F[w] == Fo and st[w].tolist() == [sto[k] for k in FIELDS]
+    # PartialCol with the same launch shape
+    S, f, F, st = run_gpu_ls(plse, G, P, 5, 9, iters, 31, plse.LS_REPAIR | plse.LS_PARTIALCOL)
+    for w in range(0, count, 3):
+        So, Fo, sto = oracle_ls(I, P[w], 5 + w, 9, iters, 31, plse.LS_REPAIR | plse.LS_PARTIALCOL)
+        assert np.array_equal(S[w], So) and F[w] == Fo
