@@ -1,0 +1,348 @@
+"""Benchmark: tabu moves/s of the MPMA hot path on GB300.
+
+Workload (one "step" = one generation of Alg. 2 on each instance):
+  five synthetic n = 70 PLSE instances with fill ratio r in {0.3, 0.4, 0.5, 0.6,
+  0.7} (random insertion for 0.3/0.5/0.7, permuted cyclic square for 0.4/0.6;
+  seeds 3000+k), population p = 16384, phase-1 tabu iterations 10|V|, phase 2
+  2|V| iterations, Philox seed 1 (+ rank).  The populations stay resident on the
+  GPU between steps; the optimality stop is off so every step is a full
+  generation.  Warm-up generations run first, so the timed generations are
+  steady-state ones (walks start from AUX offspring, as in the paper's runs).
+
+Default: python bench.py  (N=1, 5 timed steps, 3 warm-up steps)
+Multi-GPU: torchrun ... bench.py --gpus N  (independent replicas, one per rank)
+Reference arm: python bench.py --impl reference  (the CPU oracle on a bounded
+sample of the same workload, on the host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RATIOS = (0.3, 0.4, 0.5, 0.6, 0.7)
+POP = 16384
+METRIC = "tabu moves/s (16k pop, n=70)"
+UNIT = "moves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--pop", type=int, default=POP)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(pop, iters_note="10|V|"):
+    return {"workload": "n70_r0.3-0.7_p%d" % pop, "n": 70, "fill_ratios": list(RATIOS),
+            "instances": len(RATIOS), "population": pop, "phase1_iters": iters_note,
+            "phase2_iters": "2|V|", "generations_per_step": 1, "seed": 1,
+            "l2": "inputs larger than L2: five resident populations (colourings, bit planes, "
+                  "scores) of about 0.5 GB in total are touched every step",
+            "optimal_stop": False}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+def walk_bytes(w):
+    """Algorithmic bytes of tabu moves (explicit-gamma accounting): per scanned
+    candidate 1 B colour, per scanned (v, j) pair 1 B gamma + 2 B tabu expiry,
+    per applied move 5 B per neighbour of v* (colour read + two gamma updates)
+    plus a 1 B colour write and a 2 B expiry write."""
+    return w["cand"] + 3 * w["pairs"] + 5 * w["deg"] + 3 * w["moves"]
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as tdist
+    from paper_2103_10453_gb300 import inputs, plse
+
+    rank, world, local = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    seed = 1 + rank
+
+    grids = [inputs.n70(r) for r in RATIOS]
+    insts = []
+    for g in grids:
+        G = plse.Instance(g)
+        prm = plse.default_params(stop_at_bound=0)
+        G.set_params(prm)
+        G.run_begin(args.pop, args.warmup + args.steps + 1, 10 * G.nv, seed)
+        insts.append(G)
+
+    def step():
+        for G in insts:
+            G.run_step(1)
+
+    for _ in range(args.warmup):
+        step()
+    before = [G.run_result() for G in insts]
+
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        tdist.barrier()
+    after = [G.run_result() for G in insts]
+
+    moves = sum(a["walks"]["moves"] - b["walks"]["moves"] for a, b in zip(after, before))
+    wdelta = {k: sum(a["walks"][k] - b["walks"][k] for a, b in zip(after, before))
+              for k in ("iterations", "moves", "cand", "pairs", "deg")}
+    ls_ms = sum(a["ms_local_search"] - b["ms_local_search"] for a, b in zip(after, before))
+    launches = sum(a["launches"] - b["launches"] for a, b in zip(after, before))
+    per_inst = []
+    for r, a, b in zip(RATIOS, after, before):
+        mv = a["walks"]["moves"] - b["walks"]["moves"]
+        it = a["walks"]["iterations"] - b["walks"]["iterations"]
+        per_inst.append({"r": r, "nv": insts[RATIOS.index(r)].nv, "moves": mv,
+                         "ls_ms": round(a["ms_local_search"] - b["ms_local_search"], 2),
+                         "cand_per_iter": round((a["walks"]["cand"] - b["walks"]["cand"]) / max(it, 1), 2),
+                         "best_score": a["score"]})
+
+    # max over ranks of the timed region; sum of the work
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    mv = torch.tensor([float(moves)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(mv, op=tdist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    total_moves = float(mv.item())
+    value = total_moves / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the local search), live from this run
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    smem_peak = sm_count * 128 * sm_max * 1e6 / 1e9          # GB/s
+    bytes_alg = walk_bytes(wdelta)
+    launches_ls = len(insts) * args.steps
+    achieved = bytes_alg / (ls_ms / 1e3) / 1e9 if ls_ms > 0 else None
+    roofline = {"bound": "smem", "achieved": round(achieved, 1) if achieved else None,
+                "peak": round(smem_peak, 1), "unit": "GB/s",
+                "frac": round(achieved / smem_peak, 4) if achieved else None,
+                "traffic": None,
+                "kernel": "local_search_kernel",
+                "peak_source": "derived: %d SMs x 128 B/clk x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
+                               % (sm_count, sm_max),
+                "bytes_per_launch": round(bytes_alg / launches_ls),
+                "ms_per_launch": round(ls_ms / launches_ls, 3),
+                "moves_per_launch": round(wdelta["moves"] / launches_ls)}
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+           "data": "synthetic (seeded instances of the paper's benchmark shapes; random initial colourings)",
+           "config": dict(workload_config(args.pop), parallelism="replicas" if world > 1 else "single"),
+           "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+           "per_instance": per_inst}
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = run_e2e(args, plse, inputs, seed)
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(sample_seconds=20.0)
+    for G in insts:
+        G.close()
+    if world > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(args, plse, inputs, seed):
+    """Same metric through the public C ABI with host buffers: plse_create
+    (host grid -> device), one-generation plse_solve_ex per instance, best grid
+    back to the host; wall clock around all of it."""
+    import numpy as np
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    moves, h2d, d2h = 0, 0, 0
+    for r in RATIOS:
+        g = np.ascontiguousarray(inputs.n70(r), dtype=np.int8)
+        G = plse.Instance(g)
+        G.set_params(plse.default_params(stop_at_bound=0))
+        res = G.solve(args.pop, 1, 10 * G.nv, seed, with_stats=True)
+        moves += res["walks"]["moves"]
+        h2d += g.nbytes + G.nv * 24 + 2 * 70 * 20          # grid + uploaded instance image
+        d2h += res["best_grid"].nbytes + 8 * res["generations"] + 64
+        G.close()
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"value": round(moves / secs, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "note": "one generation (from random colourings) of each of the five instances, "
+                    "host grid in, host best grid out, wall clock"}
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(per_instance=1, budget_s=20.0):
+    """The CPU oracle as it stands on a bounded sample of the workload: for each
+    instance, one individual is brought to a steady state by an untimed
+    two-phase walk from a random colouring, then one generation's local search
+    (phase 1 with 10|V| iterations, phase 2, repair) of that individual is timed.
+    Returns (moves, seconds, description)."""
+    import oracle
+    from paper_2103_10453_gb300 import inputs
+    oracle.build()
+    moves, secs = 0, 0.0
+    for r in RATIOS:
+        I = oracle.Instance(inputs.n70(r))
+        for i in range(per_instance):
+            P = I.init_population(1, 1)
+            S, _, _ = I.tabu_walk(P[0], i, 0, 1, 10 * I.nv, 1)
+            S, _, _ = I.tabu_walk(S, i, 0, 2, 2 * I.nv, 1)
+            S, _ = I.repair(S)
+            t0 = time.perf_counter()
+            S1, _, st1 = I.tabu_walk(S, i, 1, 1, 10 * I.nv, 1)
+            S2, _, st2 = I.tabu_walk(S1, i, 1, 2, 2 * I.nv, 1)
+            I.repair(S2)
+            secs += time.perf_counter() - t0
+            moves += st1["moves"] + st2["moves"]
+        if secs > budget_s:
+            break
+    desc = ("one steady-state generation of local search (phase 1 10|V| + phase 2 2|V| + repair) "
+            "for %d individual(s) of each n=70 instance, single-threaded C oracle" % per_instance)
+    return moves, secs, desc
+
+
+def cpu_baseline(sample_seconds=20.0):
+    moves, secs, desc = oracle_sample(1, sample_seconds)
+    return {"value": round(moves / secs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": desc, "seconds": round(secs, 2)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    vals, total_m, total_s = [], 0, 0.0
+    desc = ""
+    for _ in range(args.warmup):
+        oracle_sample(1, 5.0)
+    for _ in range(args.steps):
+        m, s, desc = oracle_sample(1, 10.0)
+        vals.append(m / s)
+        total_m += m
+        total_s += s
+    value = total_m / total_s
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * total_s / args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+           "data": "synthetic (seeded instances of the paper's benchmark shapes)",
+           "config": workload_config(args.pop), "impl": "reference",
+           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

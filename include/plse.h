@@ -57,6 +57,8 @@ typedef struct {
     int32_t matching;              /* PLSE_MATCH_NEAREST or PLSE_MATCH_RANDOM    */
     int32_t crossover;             /* PLSE_XOVER_AUX or PLSE_XOVER_UX            */
     int32_t tested_cap;            /* tested-partner list capacity, 1..256 (64)  */
+    int32_t stop_at_bound;         /* 1: stop once f(S*) reaches the bound (Sec. 3.2);
+                                      0: keep running the requested generations   */
 } plse_params;
 
 #define PLSE_MODE_PLITS       0    /* two-phase tabu search, Sec. 3.3            */
@@ -80,6 +82,7 @@ typedef struct {
     plse_walk_stats walks;    /* summed over every walk of the run              */
     double  ms_total;         /* device time of the whole run (CUDA events)     */
     double  ms_local_search;  /* device time of the local-search launches       */
+    int64_t launches;         /* kernels launched by the run                    */
 } plse_solve_stats;
 
 /* ---- instance -------------------------------------------------------------
@@ -132,6 +135,20 @@ int  plse_solve(plse_handle h, int pop, int generations, int64_t iters, uint64_t
 int  plse_solve_ex(plse_handle h, int pop, int generations, int64_t iters, uint64_t seed,
                    void *stream, int8_t *best_grid, int *best_score,
                    plse_solve_stats *stats);
+
+/* ---- resumable run: the population stays resident on the device ----------
+ * plse_run_begin initialises a run of Alg. 2 (population P_0, S* empty) with
+ * room for `max_generations`; plse_run_step executes up to `generations` more
+ * generations on `stream` (blocking; *done (may be NULL) is set once the run has
+ * stopped at the bound or used its generations); plse_run_result copies the
+ * best grid, score and statistics of the run so far.  plse_solve is
+ * begin + step + result.  One run per handle at a time; a new begin discards
+ * the previous run. */
+int  plse_run_begin(plse_handle h, int pop, int max_generations, int64_t iters, uint64_t seed,
+                    void *stream);
+int  plse_run_step(plse_handle h, int generations, void *stream, int *done);
+int  plse_run_result(plse_handle h, void *stream, int8_t *best_grid, int *best_score,
+                     plse_solve_stats *stats, int32_t *trace);
 
 /* ---- step entry points (device buffers, asynchronous on `stream`) ---------
  * plse_init_population -- Sec. 3.2: P[i][v] uniform over D(v)\{0}, individual

@@ -167,7 +167,7 @@ int check_params(plse_instance *h, const plse_params &p)
         (p.mode != PLSE_MODE_PLITS && p.mode != PLSE_MODE_PARTIALCOL) ||
         (p.matching != PLSE_MATCH_NEAREST && p.matching != PLSE_MATCH_RANDOM) ||
         (p.crossover != PLSE_XOVER_AUX && p.crossover != PLSE_XOVER_UX) ||
-        p.tested_cap < 1 || p.tested_cap > 256)
+        p.tested_cap < 1 || p.tested_cap > 256 || (p.stop_at_bound != 0 && p.stop_at_bound != 1))
         return fail(h, PLSE_EINVAL, "parameter out of range");
     return PLSE_OK;
 }
@@ -248,9 +248,9 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.F_out = F_out;
     a.stats = stats;
     a.skip = skip;
-    LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_warps > 0 ? h->ls_warps : default_ls_warps(h->di));
+    LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_warps);
     if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "local search does not fit on this device");
-    int rc = ensure_ls_workspace(h, L.blocks);
+    int rc = ensure_ls_workspace(h, L.slots());
     if (rc) return rc;
     a.G = h->ws.G;
     a.slot_clock = h->ws.slot_clock;
@@ -298,6 +298,7 @@ void plse_default_params(plse_params *p)
     p->matching = PLSE_MATCH_NEAREST;
     p->crossover = PLSE_XOVER_AUX;
     p->tested_cap = 64;
+    p->stop_at_bound = 1;
 }
 
 int plse_create(int n, const int8_t *grid, plse_handle *out)

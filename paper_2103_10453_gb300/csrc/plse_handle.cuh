@@ -22,6 +22,17 @@ struct Workspace {
     size_t counters_cap = 0;
 };
 
+// one resumable run of Alg. 2 (plse_run_begin / plse_run_step / plse_run_result)
+struct Session {
+    int active = 0, finished = 0;
+    int pop = 0, max_gens = 0, gen = 0, cur = 0;
+    int64_t iters = 0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    double ms_ls = 0;
+    long long launches = 0;
+};
+
 }  // namespace plse
 
 struct plse_instance {
@@ -41,6 +52,7 @@ struct plse_instance {
     plse::DevInst di{};
     plse::Workspace ws;
     plse::SolverState *solver = nullptr;
+    plse::Session session;
     uint32_t *step_planes = nullptr;   // bit planes for the population step entry points
     size_t step_planes_cap = 0;
     plse::PopScratch step_ps;          // Alg. 4 scratch for plse_pop_update

@@ -61,25 +61,28 @@ struct LSArgs {
 };
 
 struct LSLaunch {
-    int blocks;        // one walk slot per block (persistent over walks)
-    int warps;         // warps per block working on one walk (1, 2, 4 or 8)
+    int blocks;        // persistent blocks (one per SM at most)
+    int warps;         // warps per walk (1, 2, 4 or 8)
+    int walks;         // concurrent walks per block, each with its own shared-memory slot
     size_t smem;       // dynamic shared memory per block
     int colour_words;  // 32-bit words of a colour mask actually used (1..4)
+    int slots() const { return blocks * walks; }
 };
 
-// Shared-memory plan of one walk slot (bytes).
+// Shared-memory plan of one block (bytes): instance part, then `walks` slots.
 struct SmemPlan {
-    size_t off_rc, off_allow, off_S, off_B, off_R, off_K, off_RP, off_KP, off_cmask, off_clist,
-        off_tc, off_red, total;
+    size_t inst;       // vertex coordinates and allowed-colour masks
+    size_t slot;       // one walk: colouring, count planes, candidate set, tabu cache, scalars
+    size_t off_S, off_RP, off_KP, off_cmask, off_lmask, off_list, off_tc, off_red;   // within a slot
+    size_t total(int walks) const { return inst + slot * (size_t)walks; }
 };
-SmemPlan smem_plan(const DevInst &I);
 
 // Launchers (return cudaError_t of the launch; asynchronous).
 cudaError_t launch_init_population(const DevInst &I, int pop, uint64_t seed, uint8_t *P,
                                    cudaStream_t st);
 cudaError_t launch_local_search(const DevInst &I, const LSArgs &a, const LSLaunch &L,
                                 cudaStream_t st);
-LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps);
-int default_ls_warps(const DevInst &I);
+// warps = 0: automatic.  max_walks caps the walks per block (0 = no cap).
+LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps, int max_walks = 0);
 
 }  // namespace plse

@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(32) eval_kernel(const DevInst I, const uint8_t
 }
 
 // Alg. 2: S'* = argmin f over the (legal) offspring, S* replaced if strictly better
-__global__ void __launch_bounds__(1024) best_kernel(int p, int nv, int ftarget, int gen,
+__global__ void __launch_bounds__(1024) best_kernel(int p, int nv, int ftarget, int gen, int stop_at_bound,
                                                     const int32_t *fprime, const uint8_t *Pp,
                                                     const plse_walk_stats *ws, int64_t *e_p,
                                                     Ctrl *ctrl, uint8_t *Sstar, int32_t *trace)
 {
-    if (ctrl->done) return;
+    if (stop_at_bound && ctrl->done) return;
     __shared__ uint32_t skey[32];
     __shared__ long long sst[7][32];
     uint32_t key = 0xffffffffu;
@@ -146,7 +146,7 @@ __global__ void gather_kernel(const DevInst I, int p, int gen, const int32_t *se
                               int cap, uint8_t *Pn, uint32_t *planesn, int64_t *en, uint32_t *uidn,
                               uint32_t *testedn, int32_t *tcountn, const int *skip)
 {
-    if (*skip) return;
+    if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= p) return;
@@ -285,81 +285,124 @@ static int ensure_solver(plse_instance *h, int p, int gens)
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);       \
     } while (0)
 
-int run_solve(plse_instance *h, int pop, int generations, int64_t iters, uint64_t seed, cudaStream_t st,
-              int8_t *best_grid, int *best_score, plse_solve_stats *stats, int32_t *trace_out)
+// kernel launches of one plse_pop_update pass over 2p candidates
+static long long pop_update_launches(int p)
 {
-    if (pop < 2 || pop > 65535 || generations < 0 || generations > 65534 || iters < 0 || iters > (1ll << 30))
-        return fail(h, PLSE_EINVAL, "plse_solve: invalid argument");
+    const int nchunks = (2 * p + kChunk - 1) / kChunk;
+    return 4 + nchunks + (nchunks - 1);
+}
+
+int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uint64_t seed, cudaStream_t st)
+{
+    if (pop < 2 || pop > 65535 || max_generations < 0 || max_generations > 65534 || iters < 0 ||
+        iters > (1ll << 30))
+        return fail(h, PLSE_EINVAL, "plse_run_begin: invalid argument");
+    Session &se = h->session;
+    se = Session();
+    se.pop = pop;
+    se.iters = iters;
+    se.seed = seed;
+    se.max_gens = max_generations;
+    se.stream = st;
+    se.active = 1;
+    const int nv = h->nv;
+    const int ftarget = h->l == 1 ? 1 : 0;
+    se.finished = (nv == 0 || nv <= ftarget || max_generations == 0);
+    if (se.finished) return PLSE_OK;
+    int rc = ensure_solver(h, pop, max_generations);
+    if (rc) return rc;
+    SolverState *s = h->solver;
+    const DevInst &I = h->di;
+    const int p = pop;
+    const size_t PV = (size_t)p * nv;
+    CK(cudaEventRecord(s->ev[0], st));
+    // P_0, its scores, planes, ids; S^O = P_0; S* = empty colouring, f* = |V|
+    CK(launch_init_population(I, p, seed, s->Pall[0], st));
+    const size_t cnt_smem = 2 * (size_t)I.n * I.n1p;
+    eval_kernel<<<std::min(p, 65535), 32, cnt_smem, st>>>(I, s->Pall[0], p, s->e[0]);
+    CK(cudaGetLastError());
+    CK(launch_planes(I, s->Pall[0], p, s->planes[0], st));
+    init_ids_kernel<<<(p + 255) / 256, 256, 0, st>>>(p, s->uid[0], s->tcount[0]);
+    init_ctrl_kernel<<<1, 1, 0, st>>>(s->ctrl, nv, ftarget);
+    CK(cudaMemsetAsync(s->Sstar, 0, (size_t)nv, st));
+    CK(cudaMemcpyAsync(s->SO, s->Pall[0], PV, cudaMemcpyDeviceToDevice, st));
+    CK(cudaGetLastError());
+    se.launches += 6;
+    se.cur = 0;
+    se.gen = 0;
+    return PLSE_OK;
+}
+
+int run_step(plse_instance *h, int generations, cudaStream_t st, int *done_out)
+{
+    Session &se = h->session;
+    if (!se.active) return fail(h, PLSE_EINVAL, "plse_run_step: no run in progress");
+    if (generations < 0) return fail(h, PLSE_EINVAL, "plse_run_step: invalid argument");
     const DevInst &I = h->di;
     const plse_params &prm = h->params;
     const int nv = h->nv;
     const int ftarget = h->l == 1 ? 1 : 0;
-    int fstar = nv, gens_done = 0;
-    std::vector<uint8_t> Sstar_h((size_t)nv, 0);
-    double ms_total = 0, ms_ls = 0;
-    long long wst[7] = {0, 0, 0, 0, 0, 0, 0};
-
-    if (nv > 0 && fstar > ftarget && generations > 0) {
-        int rc = ensure_solver(h, pop, generations);
-        if (rc) return rc;
+    for (int k = 0; k < generations && !se.finished; ++k) {
+        if (se.gen >= se.max_gens) { se.finished = 1; break; }
         SolverState *s = h->solver;
-        const int p = pop, cap = prm.tested_cap;
+        const int p = se.pop, cap = prm.tested_cap, g = se.gen, cur = se.cur, nxt = cur ^ 1;
         const size_t PV = (size_t)p * nv, stride = (size_t)I.nw * I.nb;
-        CK(cudaEventRecord(s->ev[0], st));
-        // P_0, its scores, planes, ids; S^O = P_0; S* = empty colouring, f* = |V|
-        CK(launch_init_population(I, p, seed, s->Pall[0], st));
-        const size_t cnt_smem = 2 * (size_t)I.n * I.n1p;
-        eval_kernel<<<std::min(p, 65535), 32, cnt_smem, st>>>(I, s->Pall[0], p, s->e[0]);
-        CK(cudaGetLastError());
-        CK(launch_planes(I, s->Pall[0], p, s->planes[0], st));
-        init_ids_kernel<<<(p + 255) / 256, 256, 0, st>>>(p, s->uid[0], s->tcount[0]);
-        init_ctrl_kernel<<<1, 1, 0, st>>>(s->ctrl, nv, ftarget);
-        CK(cudaMemsetAsync(s->Sstar, 0, (size_t)nv, st));
-        CK(cudaMemcpyAsync(s->SO, s->Pall[0], PV, cudaMemcpyDeviceToDevice, st));
-        CK(cudaGetLastError());
-        const int *skip = &s->ctrl->done;
+        const int *skip = prm.stop_at_bound ? &s->ctrl->done : nullptr;
         const int flags = prm.mode == PLSE_MODE_PARTIALCOL ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
                                                            : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
-        int cur = 0;
-        for (int g = 0; g < generations; ++g) {
-            const int nxt = cur ^ 1;
-            uint8_t *Pp = s->Pall[cur] + PV;
-            CK(cudaEventRecord(s->ev[1], st));
-            rc = enqueue_local_search(h, s->SO, Pp, p, 0, g, iters, seed, flags, s->fprime, nullptr,
+        uint8_t *Pp = s->Pall[cur] + PV;
+        CK(cudaEventRecord(s->ev[1], st));
+        int rc = enqueue_local_search(h, s->SO, Pp, p, 0, g, se.iters, se.seed, flags, s->fprime, nullptr,
                                       s->wstats, st, skip);
-            if (rc) return rc;
-            CK(cudaEventRecord(s->ev[2], st));
-            best_kernel<<<1, 1024, 0, st>>>(p, nv, ftarget, g, s->fprime, Pp, s->wstats, s->e[cur] + p,
-                                            s->ctrl, s->Sstar, s->trace);
-            CK(cudaGetLastError());
-            // the stop test needs f* on the host: one 8-byte read per generation
-            int hc[2];
-            CK(cudaMemcpyAsync(hc, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, s->ev[1], s->ev[2]));
-            ms_ls += ms;
-            gens_done = g + 1;
-            if (hc[1]) break;
-            CK(launch_planes(I, Pp, p, s->planes[cur] + (size_t)p * stride, st));
-            CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel,
-                                 nullptr, skip, st));
-            gather_kernel<<<(p * 32 + 255) / 256, 256, 0, st>>>(
-                I, p, g, s->sel, s->Pall[cur], s->planes[cur], s->e[cur], s->uid[cur], s->tested[cur],
-                s->tcount[cur], cap, s->Pall[nxt], s->planes[nxt], s->e[nxt], s->uid[nxt],
-                s->tested[nxt], s->tcount[nxt], skip);
-            CK(cudaGetLastError());
-            CK(launch_matching(I, p, s->planes[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], cap,
-                               prm.matching == PLSE_MATCH_RANDOM, g, seed, s->partner, s->dist, skip, st));
-            CK(launch_crossover(I, p, s->Pall[nxt], s->partner, s->dist, g, seed, prm.beta,
-                                prm.crossover == PLSE_XOVER_UX, s->SO, skip, st));
-            cur = nxt;
-        }
+        if (rc) return rc;
+        CK(cudaEventRecord(s->ev[2], st));
+        best_kernel<<<1, 1024, 0, st>>>(p, nv, ftarget, g, prm.stop_at_bound, s->fprime, Pp, s->wstats,
+                                        s->e[cur] + p, s->ctrl, s->Sstar, s->trace);
+        CK(cudaGetLastError());
+        se.launches += 2;
+        // the stop test needs f* on the host: one 8-byte read per generation
+        int hc[2];
+        CK(cudaMemcpyAsync(hc, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, s->ev[1], s->ev[2]));
+        se.ms_ls += ms;
+        se.gen = g + 1;
+        if (prm.stop_at_bound && hc[1]) { se.finished = 1; break; }
+        CK(launch_planes(I, Pp, p, s->planes[cur] + (size_t)p * stride, st));
+        CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st));
+        gather_kernel<<<(p * 32 + 255) / 256, 256, 0, st>>>(
+            I, p, g, s->sel, s->Pall[cur], s->planes[cur], s->e[cur], s->uid[cur], s->tested[cur], s->tcount[cur],
+            cap, s->Pall[nxt], s->planes[nxt], s->e[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], skip);
+        CK(cudaGetLastError());
+        CK(launch_matching(I, p, s->planes[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], cap,
+                           prm.matching == PLSE_MATCH_RANDOM, g, se.seed, s->partner, s->dist, skip, st));
+        CK(launch_crossover(I, p, s->Pall[nxt], s->partner, s->dist, g, se.seed, prm.beta,
+                            prm.crossover == PLSE_XOVER_UX, s->SO, skip, st));
+        se.launches += 1 + pop_update_launches(p) + 3;
+        se.cur = nxt;
+    }
+    if (done_out) *done_out = se.finished;
+    return PLSE_OK;
+}
+
+int run_result(plse_instance *h, cudaStream_t st, int8_t *best_grid, int *best_score, plse_solve_stats *stats,
+               int32_t *trace_out)
+{
+    Session &se = h->session;
+    if (!se.active) return fail(h, PLSE_EINVAL, "plse_run_result: no run in progress");
+    const int nv = h->nv, n = h->n;
+    int fstar = nv, gens_done = 0;
+    std::vector<uint8_t> Sstar_h((size_t)nv, 0);
+    double ms_total = 0;
+    long long wst[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (h->solver && se.gen > 0) {
+        SolverState *s = h->solver;
         CK(cudaEventRecord(s->ev[3], st));
         Ctrl hctrl;
         CK(cudaMemcpyAsync(&hctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(Sstar_h.data(), s->Sstar, (size_t)nv, cudaMemcpyDeviceToHost, st));
-        if (trace_out) CK(cudaMemcpyAsync(trace_out, s->trace, sizeof(int32_t) * gens_done, cudaMemcpyDeviceToHost, st));
+        if (nv) CK(cudaMemcpyAsync(Sstar_h.data(), s->Sstar, (size_t)nv, cudaMemcpyDeviceToHost, st));
+        if (trace_out) CK(cudaMemcpyAsync(trace_out, s->trace, sizeof(int32_t) * se.gen, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         float mt = 0;
         CK(cudaEventElapsedTime(&mt, s->ev[0], s->ev[3]));
@@ -367,7 +410,6 @@ int run_solve(plse_instance *h, int pop, int generations, int64_t iters, uint64_
         fstar = hctrl.fstar;
         gens_done = hctrl.gens;
         for (int k = 0; k < 7; ++k) wst[k] = hctrl.stats[k];
-        // device-side consistency checks of the local search
         int flag = 0;
         CK(cudaMemcpy(&flag, h->ws.counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
         if (flag) {
@@ -375,7 +417,6 @@ int run_solve(plse_instance *h, int pop, int generations, int64_t iters, uint64_
             return fail(h, PLSE_ECHECK, "a local-search consistency check failed");
         }
     }
-    const int n = h->n;
     if (best_grid) {
         memcpy(best_grid, h->grid.data(), (size_t)n * n);
         for (int v = 0; v < nv; ++v) best_grid[h->cell[v]] = (int8_t)Sstar_h[v];
@@ -387,9 +428,20 @@ int run_solve(plse_instance *h, int pop, int generations, int64_t iters, uint64_
         int64_t *w = &stats->walks.iterations;
         for (int k = 0; k < 7; ++k) w[k] = wst[k];
         stats->ms_total = ms_total;
-        stats->ms_local_search = ms_ls;
+        stats->ms_local_search = se.ms_ls;
+        stats->launches = se.launches;
     }
     return PLSE_OK;
+}
+
+int run_solve(plse_instance *h, int pop, int generations, int64_t iters, uint64_t seed, cudaStream_t st,
+              int8_t *best_grid, int *best_score, plse_solve_stats *stats, int32_t *trace_out)
+{
+    int rc = run_begin(h, pop, generations, iters, seed, st);
+    if (!rc) rc = run_step(h, generations, st, nullptr);
+    if (!rc) rc = run_result(h, st, best_grid, best_score, stats, trace_out);
+    h->session.active = 0;
+    return rc;
 }
 
 int ensure_step_planes(plse_instance *h, size_t individuals)
@@ -421,6 +473,25 @@ int plse_solve_ex(plse_handle h, int pop, int generations, int64_t iters, uint64
     if (!h) return PLSE_EINVAL;
     return run_solve(h, pop, generations, iters, seed, (cudaStream_t)stream, best_grid, best_score, stats,
                      nullptr);
+}
+
+int plse_run_begin(plse_handle h, int pop, int max_generations, int64_t iters, uint64_t seed, void *stream)
+{
+    if (!h) return PLSE_EINVAL;
+    return run_begin(h, pop, max_generations, iters, seed, (cudaStream_t)stream);
+}
+
+int plse_run_step(plse_handle h, int generations, void *stream, int *done)
+{
+    if (!h) return PLSE_EINVAL;
+    return run_step(h, generations, (cudaStream_t)stream, done);
+}
+
+int plse_run_result(plse_handle h, void *stream, int8_t *best_grid, int *best_score, plse_solve_stats *stats,
+                    int32_t *trace)
+{
+    if (!h) return PLSE_EINVAL;
+    return run_result(h, (cudaStream_t)stream, best_grid, best_score, stats, trace);
 }
 
 int plse_distances(plse_handle h, const uint8_t *A, int na, const uint8_t *B, int nb, int32_t *D, void *stream)

@@ -34,7 +34,7 @@ class Params(C.Structure):
     _fields_ = [(name, C.c_int32) for name in (
         "alpha_num", "alpha_den", "tenure_rand", "phase1_phi2", "phase2_phi2_per_v",
         "phase2_iter_per_v", "spacing_gamma", "beta", "mode", "matching", "crossover",
-        "tested_cap")]
+        "tested_cap", "stop_at_bound")]
 
 
 class WalkStats(C.Structure):
@@ -50,7 +50,7 @@ WALK_STATS_FIELDS = [k for k, _ in WalkStats._fields_]
 
 class SolveStats(C.Structure):
     _fields_ = [("generations", C.c_int32), ("best_f", C.c_int32), ("walks", WalkStats),
-                ("ms_total", C.c_double), ("ms_local_search", C.c_double)]
+                ("ms_total", C.c_double), ("ms_local_search", C.c_double), ("launches", C.c_int64)]
 
 
 _lib = None
@@ -71,6 +71,9 @@ SIGNATURES = {
     "plse_solve": (C.c_int, [_vp, C.c_int, C.c_int, _i64, _u64, _vp, C.POINTER(C.c_int)]),
     "plse_solve_ex": (C.c_int, [_vp, C.c_int, C.c_int, _i64, _u64, _vp, _vp, C.POINTER(C.c_int),
                                 C.POINTER(SolveStats)]),
+    "plse_run_begin": (C.c_int, [_vp, C.c_int, C.c_int, _i64, _u64, _vp]),
+    "plse_run_step": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
+    "plse_run_result": (C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int), C.POINTER(SolveStats), _vp]),
     "plse_init_population": (C.c_int, [_vp, C.c_int, _u64, _vp, _vp]),
     "plse_local_search": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _i64, _u64, C.c_int,
                                     _vp, _vp, _vp, _vp]),
@@ -192,7 +195,30 @@ class Instance:
         if with_stats:
             out.update(generations=int(st.generations), best_f=int(st.best_f),
                        walks=st.walks.as_dict(), ms_total=float(st.ms_total),
-                       ms_local_search=float(st.ms_local_search))
+                       ms_local_search=float(st.ms_local_search), launches=int(st.launches))
+        return out
+
+    # ---- resumable run ---------------------------------------------------
+    def run_begin(self, pop, max_generations, iters, seed, stream=None):
+        self._check(self.lib.plse_run_begin(self.h, pop, max_generations, int(iters), seed, _stream(stream)))
+
+    def run_step(self, generations=1, stream=None) -> bool:
+        done = C.c_int()
+        self._check(self.lib.plse_run_step(self.h, generations, _stream(stream), C.byref(done)))
+        return bool(done.value)
+
+    def run_result(self, stream=None, trace=False):
+        grid = np.zeros((self.n, self.n), dtype=np.int8)
+        score = C.c_int()
+        st = SolveStats()
+        tr = np.zeros(65535, dtype=np.int32) if trace else None
+        self._check(self.lib.plse_run_result(self.h, _stream(stream), grid.ctypes.data, C.byref(score),
+                                             C.byref(st), tr.ctypes.data if trace else None))
+        out = {"best_grid": grid, "score": int(score.value), "generations": int(st.generations),
+               "best_f": int(st.best_f), "walks": st.walks.as_dict(), "ms_total": float(st.ms_total),
+               "ms_local_search": float(st.ms_local_search), "launches": int(st.launches)}
+        if trace:
+            out["trace"] = tr[:st.generations].copy()
         return out
 
     # ---- steps (device tensors) ------------------------------------------

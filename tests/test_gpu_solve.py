@@ -87,3 +87,30 @@ def test_edge_instances(plse, oracle_mod):
     out = G.solve(4, 3, 10, 1, with_stats=True)
     assert out["score"] == 36 and out["generations"] == 0
     assert np.array_equal(out["best_grid"], L)
+
+
+def test_resumable_run_matches_solve(plse, oracle_mod):
+    grid = inputs.random_insertion(16, 0.75, 8)
+    G, I = plse.Instance(grid), oracle_mod.Instance(grid)
+    ref = I.solve(40, 6, 120, 9)
+    G.run_begin(40, 6, 120, 9)
+    for _ in range(6):
+        if G.run_step(1):
+            break
+    res = G.run_result(trace=True)
+    assert res["score"] == ref["score"] and np.array_equal(res["best_grid"], ref["best_grid"])
+    assert res["generations"] == ref["generations"] and res["walks"] == ref["stats"]
+    assert res["trace"].tolist() == ref["trace"].tolist()
+
+
+def test_no_stop_at_bound_keeps_generating(plse, oracle_mod):
+    # the bound is reached in generation 1; with the stop disabled the run goes on
+    grid = inputs.tiny_n10()
+    G, I = plse.Instance(grid), oracle_mod.Instance(grid)
+    ref = I.solve(32, 5, 300, 2)
+    G.set_params(plse.default_params(stop_at_bound=0))
+    res = G.solve(32, 5, 300, 2, with_stats=True)
+    assert res["generations"] == 5 and ref["generations"] == 1
+    assert res["score"] == ref["score"] == 100
+    g = res["best_grid"]
+    assert is_partial_latin(g) and int((g != 0).sum()) == 100
