@@ -177,6 +177,27 @@ int  plse_local_search(plse_handle h, const uint8_t *S_in, uint8_t *S_out, int c
                        int ind0, int gen, int64_t iters, uint64_t seed, int flags,
                        int32_t *f_out, int64_t *F_out, plse_walk_stats *stats, void *stream);
 
+/* plse_local_search_noalloc -- plse_local_search for callers that cannot
+ * allocate device memory at call time (an application whose device memory is
+ * reserved up front by its own pool allocator, or a latency-critical loop that
+ * must not pay the implicit device-wide synchronisation of cudaMalloc/cudaFree).
+ * The paper has no counterpart: it is a deployment variant of Alg. 3.  Same
+ * arguments, outputs and results as plse_local_search; it calls no cudaMalloc,
+ * cudaFree or allocating routine.  Its scratch is a fixed 16 MiB array inside
+ * the library on every GPU that loads it (held until exit), which bounds the
+ * concurrent walks to (16 MiB - 256 B) / (4*|V|*n1p + 4) (n1p = n + 1 rounded up
+ * to a multiple of 4): fewer walks in flight than plse_local_search uses on
+ * large instances, same results.  PLSE_ENOTSUP if not even one walk fits.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Calls share
+ * the array: each clears the part it uses, and calls whose work overlaps on the
+ * GPU (e.g. on two streams) race.  Device-side check failures of this entry
+ * point are recorded in the array, not reported by plse_sync. */
+int  plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uint8_t *S_out, int count,
+                               int ind0, int gen, int64_t iters, uint64_t seed, int flags,
+                               int32_t *f_out, int64_t *F_out, plse_walk_stats *stats,
+                               void *stream);
+
 /* plse_distances -- Sec. 3.4, Eq. 9: D[a*nb + b] = #v with A_a(v) != B_b(v).
  * A: device uint8 [na*nv], B: device uint8 [nb*nv], D: device int32 [na*nb]. */
 int  plse_distances(plse_handle h, const uint8_t *A, int na, const uint8_t *B, int nb,

@@ -77,6 +77,8 @@ SIGNATURES = {
     "plse_init_population": (C.c_int, [_vp, C.c_int, _u64, _vp, _vp]),
     "plse_local_search": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _i64, _u64, C.c_int,
                                     _vp, _vp, _vp, _vp]),
+    "plse_local_search_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _i64, _u64,
+                                            C.c_int, _vp, _vp, _vp, _vp]),
     "plse_distances": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp]),
     "plse_pop_update": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "plse_matching": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, _u64, _vp, _vp, _vp]),
@@ -229,6 +231,14 @@ class Instance:
     def local_search(self, S_in, S_out, count, ind0, gen, iters, seed, flags,
                      f_out=None, F_out=None, stats=None, stream=None):
         self._check(self.lib.plse_local_search(
+            self.h, _dptr(S_in), _dptr(S_out), count, ind0, gen, int(iters), seed, flags,
+            _dptr(f_out), _dptr(F_out), _dptr(stats), _stream(stream)))
+
+    def local_search_noalloc(self, S_in, S_out, count, ind0, gen, iters, seed, flags,
+                             f_out=None, F_out=None, stats=None, stream=None):
+        """As local_search, with the library's fixed scratch array instead of
+        device memory allocated at call time (for callers that cannot allocate)."""
+        self._check(self.lib.plse_local_search_noalloc(
             self.h, _dptr(S_in), _dptr(S_out), count, ind0, gen, int(iters), seed, flags,
             _dptr(f_out), _dptr(F_out), _dptr(stats), _stream(stream)))
 
