@@ -117,8 +117,9 @@ int  plse_set_params(plse_handle h, const plse_params *p);
 int  plse_get_params(plse_handle h, plse_params *p);
 
 /* Launch knobs that never change results: warps per walk of the local-search
- * kernel (1, 2, 4 or 8; 0 = automatic from |V|).  Used by the autotuner. */
-int  plse_set_launch(plse_handle h, int ls_warps);
+ * kernel (1, 2, 4 or 8; 0 = automatic) and the cap on concurrent walks per block
+ * (0 = as many as fit in shared memory).  Used by the autotuner. */
+int  plse_set_launch(plse_handle h, int ls_warps, int ls_walks);
 
 /* ---- whole solve (Alg. 2) ---------------------------------------------------
  * Runs `generations` generations of MPMA with population `pop` (2..65535) and

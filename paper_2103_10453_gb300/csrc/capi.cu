@@ -185,6 +185,19 @@ int check_exactness(plse_instance *h, const plse_params &p)
     return PLSE_OK;
 }
 
+// ceil(2^32 / d) if floor(x / d) == high word of x * that for every x the
+// tenure formula can produce (x <= alpha_num * |V|), else 0 (the kernel divides)
+uint32_t tenure_reciprocal(int alpha_num, int alpha_den, int nv)
+{
+    if (alpha_den <= 1) return 0;
+    const uint64_t m = ((1ull << 32) + (uint64_t)alpha_den - 1) / (uint64_t)alpha_den;
+    if (m > 0xFFFFFFFFull) return 0;
+    const uint64_t xmax = (uint64_t)alpha_num * (uint64_t)nv;
+    for (uint64_t x = 0; x <= xmax; ++x)
+        if (((x * m) >> 32) != x / (uint64_t)alpha_den) return 0;
+    return (uint32_t)m;
+}
+
 int max_tenure(const plse_instance *h)
 {
     const plse_params &p = h->params;
@@ -241,6 +254,7 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.alpha_num = p.alpha_num;
     a.alpha_den = p.alpha_den;
     a.tenure_rand = p.tenure_rand;
+    a.alpha_recip = h->alpha_recip;
     const int tmax = max_tenure(h);
     a.span1 = (int)(a.iters1 + tmax + 2);
     a.span2 = (int)(a.iters2 + tmax + 2);
@@ -248,7 +262,7 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.F_out = F_out;
     a.stats = stats;
     a.skip = skip;
-    LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_warps);
+    LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_warps, h->ls_walks);
     if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "local search does not fit on this device");
     int rc = ensure_ls_workspace(h, L.slots());
     if (rc) return rc;
@@ -313,6 +327,7 @@ int plse_create(int n, const int8_t *grid, plse_handle *out)
         rc = (e != cudaSuccess) ? cuda_fail(h, e, "cudaGetDevice") : upload_instance(h);
     }
     if (rc == PLSE_OK) rc = check_exactness(h, h->params);
+    if (rc == PLSE_OK) h->alpha_recip = tenure_reciprocal(h->params.alpha_num, h->params.alpha_den, h->nv);
     if (rc != PLSE_OK) {
         plse_destroy(h);
         return rc;
@@ -357,6 +372,7 @@ int plse_set_params(plse_handle h, const plse_params *p)
     rc = check_exactness(h, *p);
     if (rc) return rc;
     h->params = *p;
+    h->alpha_recip = tenure_reciprocal(p->alpha_num, p->alpha_den, h->nv);
     return PLSE_OK;
 }
 
@@ -367,11 +383,13 @@ int plse_get_params(plse_handle h, plse_params *p)
     return PLSE_OK;
 }
 
-int plse_set_launch(plse_handle h, int ls_warps)
+int plse_set_launch(plse_handle h, int ls_warps, int ls_walks)
 {
-    if (!h || !(ls_warps == 0 || ls_warps == 1 || ls_warps == 2 || ls_warps == 4 || ls_warps == 8))
+    if (!h || !(ls_warps == 0 || ls_warps == 1 || ls_warps == 2 || ls_warps == 4 || ls_warps == 8) ||
+        ls_walks < 0 || ls_walks > 256)
         return PLSE_EINVAL;
     h->ls_warps = ls_warps;
+    h->ls_walks = ls_walks;
     return PLSE_OK;
 }
 

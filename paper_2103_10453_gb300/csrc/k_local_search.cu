@@ -59,6 +59,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
 
 __device__ __forceinline__ uint32_t bounded(uint32_t u, uint32_t k) { return __umulhi(u, k); }
 
+// floor(x / alpha_den) by the reciprocal the host checked exact over the range used
+__device__ __forceinline__ int tenure_div(const LSArgs &a, int x)
+{
+    return a.alpha_recip ? (int)__umulhi((uint32_t)x, a.alpha_recip) : x / a.alpha_den;
+}
+
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ inline int colour_words(int n) { return n < 32 ? 1 : n < 64 ? 2 : n < 96 ? 3 : 4; }
 
@@ -201,28 +207,38 @@ __device__ __forceinline__ const uint32_t *line_planes(const uint32_t *P, int cw
     return P + (size_t)line * cw * kPlanes;
 }
 
-// +1 / -1 on count[line][k] (one thread per line at a time)
-__device__ __forceinline__ void count_step(uint32_t *P, int cw, int line, int k, bool inc)
+// +1 / -1 on count[line][k] (one thread per line at a time).  Returns the change
+// in the number of counts >= 4 (planes 2..6), which selects the evaluation path.
+__device__ __forceinline__ int count_step(uint32_t *P, int cw, int line, int k, bool inc)
 {
-    uint32_t *w = P + ((size_t)line * cw + (k >> 5)) * kPlanes;
-    uint32_t carry = 1u << (k & 31);
+    uint4 *w = reinterpret_cast<uint4 *>(P + ((size_t)line * cw + (k >> 5)) * kPlanes);
+    uint4 a = w[0], b = w[1];
+    uint32_t x[7] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+    const uint32_t bit = 1u << (k & 31);
+    const int old_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
+    uint32_t carry = bit;
 #pragma unroll
     for (int p = 0; p < 7; ++p) {
-        const uint32_t x = w[p];
-        const uint32_t t = inc ? (x & carry) : (~x & carry);
-        w[p] = x ^ carry;
+        const uint32_t t = inc ? (x[p] & carry) : (~x[p] & carry);
+        x[p] ^= carry;
         carry = t;
     }
+    w[0] = make_uint4(x[0], x[1], x[2], x[3]);
+    w[1] = make_uint4(x[4], x[5], x[6], b.w);
+    const int new_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
+    return new_hi - old_hi;
 }
 
 __device__ __forceinline__ int count_of(const uint32_t *P, int cw, int line, int k)
 {
     const uint32_t *w = P + ((size_t)line * cw + (k >> 5)) * kPlanes;
+    const uint4 a = *reinterpret_cast<const uint4 *>(w);
+    const uint4 b4 = *reinterpret_cast<const uint4 *>(w + 4);
     const uint32_t b = k & 31;
-    int x = 0;
-#pragma unroll
-    for (int p = 0; p < 7; ++p) x |= (int)((w[p] >> b) & 1u) << p;
-    return x;
+    const uint32_t x = ((a.x >> b) & 1u) | (((a.y >> b) & 1u) << 1) | (((a.z >> b) & 1u) << 2) |
+                       (((a.w >> b) & 1u) << 3) | (((b4.x >> b) & 1u) << 4) | (((b4.y >> b) & 1u) << 5) |
+                       (((b4.z >> b) & 1u) << 6);
+    return (int)x;
 }
 
 __device__ __forceinline__ int gamma_of(const DevInst &I, const Ctx &c, int v, int k)
@@ -249,6 +265,14 @@ __device__ __forceinline__ void build_planes(const DevInst &I, const Ctx &c)
             if (k) count_step(T, c.cw, line, k, true);
         }
     }
+    gsync<NW>(c);
+    int hi = 0;
+    for (int t = c.gt; t < 2 * I.n * c.cw; t += 32 * NW) {
+        const uint32_t *w = c.s.RP + (size_t)t * kPlanes;
+        hi += __popc(w[2] | w[3] | w[4] | w[5] | w[6]);
+    }
+    hi = gsum<NW>(hi, c);
+    if (c.gt == 0) c.s.scal[2] = hi;
     gsync<NW>(c);
 }
 
@@ -496,6 +520,128 @@ __device__ __forceinline__ int bits_min(const uint32_t (&s)[NWC][8], const uint3
 //                  2dF(0) = 2 - mult*g_i
 // with s_j = R[r][j] + K[c][j] and g_i = gamma[v][i] (Sec. 3.3).  A move is
 // admissible if not tabu, or if 2dF < A (aspiration by the phase's best).
+// 3-plane variants, exact while every count is <= 3 (sums <= 6)
+template <int NWC>
+__device__ __forceinline__ int value3(const uint32_t (&s0)[NWC], const uint32_t (&s1)[NWC],
+                                      const uint32_t (&s2)[NWC], uint32_t k)
+{
+    uint32_t sel[NWC];
+    word_masks<NWC>(k, sel);
+    uint32_t w0 = 0, w1 = 0, w2 = 0;
+#pragma unroll
+    for (int q = 0; q < NWC; ++q) {
+        w0 |= s0[q] & sel[q];
+        w1 |= s1[q] & sel[q];
+        w2 |= s2[q] & sel[q];
+    }
+    const uint32_t b = k & 31;
+    return (int)(((w0 >> b) & 1u) | (((w1 >> b) & 1u) << 1) | (((w2 >> b) & 1u) << 2));
+}
+
+template <int NWC>
+__device__ __forceinline__ int bits_min3(const uint32_t (&s0)[NWC], const uint32_t (&s1)[NWC],
+                                         const uint32_t (&s2)[NWC], const uint32_t (&m)[NWC], int &smin)
+{
+    uint32_t set[NWC], anym = 0, any0 = 0;
+#pragma unroll
+    for (int q = 0; q < NWC; ++q) {
+        anym |= m[q];
+        set[q] = m[q] & ~(s0[q] | s1[q] | s2[q]);
+        any0 |= set[q];
+    }
+    if (!anym) return -1;
+    if (any0) {
+        smin = 0;
+    } else {
+        uint32_t val = 0;
+#pragma unroll
+        for (int q = 0; q < NWC; ++q) set[q] = m[q];
+#pragma unroll
+        for (int p = 2; p >= 0; --p) {
+            uint32_t t[NWC], anyt = 0;
+#pragma unroll
+            for (int q = 0; q < NWC; ++q) {
+                const uint32_t sp = p == 2 ? s2[q] : p == 1 ? s1[q] : s0[q];
+                t[q] = set[q] & ~sp;
+                anyt |= t[q];
+            }
+            if (anyt) {
+#pragma unroll
+                for (int q = 0; q < NWC; ++q) set[q] = t[q];
+            } else {
+                val |= 1u << p;
+            }
+        }
+        smin = (int)val;
+    }
+#pragma unroll
+    for (int q = 0; q < NWC; ++q)
+        if (set[q]) return q * 32 + __ffs(set[q]) - 1;
+    return -1;
+}
+
+// eval_vertex while all counts are <= 3: planes 0-1 of R and K only
+template <int NWC>
+__device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, const uint32_t *G, const Clock &ck,
+                                               uint32_t trel, int v, int mult, int base_unc, int A, int &pairs,
+                                               bool &slow)
+{
+    const uint2 te = c.s.tc[v];
+    const uint32_t e0 = te.x & 0xFFFFu, e1 = te.x >> 16;
+    const uint32_t c0 = te.y & 0xFFu, c1 = (te.y >> 8) & 0xFFu, em = te.y >> 16;
+    slow = em >= trel;
+    if (slow) return INT_MAX;
+    const int i = c.s.S[v];
+    const uint16_t rc = c.rc[v];
+    const int r = rc >> 8, cc = rc & 255;
+    const uint32_t *RPr = line_planes(c.s.RP, NWC, r), *KPc = line_planes(c.s.KP, NWC, cc);
+    uint32_t s0[NWC], s1[NWC], s2[NWC];
+#pragma unroll
+    for (int q = 0; q < NWC; ++q) {
+        const uint2 ra = *reinterpret_cast<const uint2 *>(RPr + q * kPlanes);
+        const uint2 ka = *reinterpret_cast<const uint2 *>(KPc + q * kPlanes);
+        const uint32_t x0 = ra.x ^ ka.x, cy = ra.x & ka.x, x1 = ra.y ^ ka.y;
+        s0[q] = x0;
+        s1[q] = x1 ^ cy;
+        s2[q] = (ra.y & ka.y) | (cy & x1);
+    }
+    const int gi = i ? value3<NWC>(s0, s1, s2, (uint32_t)i) - 2 : 0;
+    const int base2 = i ? -mult * gi : base_unc;
+    const int d2zero = 2 - mult * gi;
+    const uint4 ar = c.allow[r], ac = c.allow[I.n + cc];
+    const uint32_t ar4[4] = {ar.x, ar.y, ar.z, ar.w}, ac4[4] = {ac.x, ac.y, ac.z, ac.w};
+    uint32_t m[NWC];
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < NWC; ++q) {
+        m[q] = ar4[q] & ac4[q];
+        cnt += __popc(m[q]);
+    }
+    pairs = cnt;
+    if (i) clear_bit<NWC>(m, (uint32_t)i);
+    bool has0 = (i != 0);
+    int best = INT_MAX;
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx) {
+        const uint32_t cs = sx ? c1 : c0, es = sx ? e1 : e0;
+        if (cs == 0u) {
+            if (has0) {
+                has0 = false;
+                if (es < trel || d2zero < A) best = min(best, d2zero * kKeyScale);
+            }
+        } else if (cs < 128u && test_bit<NWC>(m, cs)) {
+            clear_bit<NWC>(m, cs);
+            const int d2 = base2 + mult * value3<NWC>(s0, s1, s2, cs);
+            if (es < trel || d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
+        }
+    }
+    if (has0) best = min(best, d2zero * kKeyScale);
+    int smin = 0;
+    const int jb = bits_min3<NWC>(s0, s1, s2, m, smin);
+    if (jb >= 0) best = min(best, (base2 + mult * smin) * kKeyScale + jb);
+    return best;
+}
+
 template <int NWC>
 __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const uint32_t *G, const Clock &ck,
                                            uint32_t trel, int v, int mult, int base_unc, int A, int &pairs)
@@ -523,7 +669,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
         }
         s[q][7] = carry;
     }
-    const int gi = i ? plane_value<NWC>(s, (uint32_t)i) - 2 : 0;
+    const int gi = i ? count_of(c.s.RP, NWC, r, i) + count_of(c.s.KP, NWC, cc, i) - 2 : 0;
     const int base2 = i ? -mult * gi : base_unc;
     const int d2zero = 2 - mult * gi;
     const uint4 ar = c.allow[r], ac = c.allow[I.n + cc];
@@ -555,7 +701,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
                 }
             } else if (cs < 128u && test_bit<NWC>(m, cs)) {
                 clear_bit<NWC>(m, cs);
-                const int d2 = base2 + mult * plane_value<NWC>(s, cs);
+                const int d2 = base2 + mult * (count_of(c.s.RP, NWC, r, (int)cs) + count_of(c.s.KP, NWC, cc, (int)cs));
                 if (es < trel || d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
             }
         }
@@ -577,7 +723,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
             while (bits) {
                 const uint32_t j = q * 32 + __ffs(bits) - 1;
                 bits &= bits - 1;
-                const int d2 = base2 + mult * plane_value<NWC>(s, j);
+                const int d2 = base2 + mult * (count_of(c.s.RP, NWC, r, (int)j) + count_of(c.s.KP, NWC, cc, (int)j));
                 const bool tabu = (j == c0) ? (e0 >= trel) : (j == c1) ? (e1 >= trel) : (Gv[j] >= tabs);
                 if (!tabu || d2 < A) best = min(best, d2 * kKeyScale + (int)j);
             }
@@ -716,6 +862,7 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         const long long A64 = F2best - F2;
         const int A = A64 < -(1LL << 30) ? -(1 << 30) : (int)A64;
 
+        const bool low = c.s.scal[2] == 0;            // every count <= 3
         unsigned long long key = kNoKey;
         int live = 0;
         for (int qq = c.gt; qq < len; qq += 32 * NW) {
@@ -723,7 +870,10 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             if (!((c.s.cmask[v >> 5] >> (v & 31)) & 1u)) continue;   // stale entry
             ++live;
             int pairs;
-            const int kv = eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs);
+            bool slow = true;
+            int kv = INT_MAX;
+            if (low) kv = eval_vertex_low<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs, slow);
+            if (slow) kv = eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs);
             st.pairs += pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, c.s.S[v]));
         }
@@ -744,56 +894,84 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         if (c.wg == 0) {
             const uint16_t rc = c.rc[v];
             const int r = rc >> 8, cc = rc & 255;
-            if (c.lane < 2) {
-                // lane 0 updates row r, lane 1 column cc: one instruction stream
-                uint32_t *P = c.lane ? c.s.KP : c.s.RP;
-                const int line = c.lane ? cc : r;
-                if (i) count_step(P, c.cw, line, i, false);
-                if (j) count_step(P, c.cw, line, j, true);
+            // count updates: lane 0 row r / colour i, lane 1 column cc / colour i,
+            // lanes 2-3 the same for colour j (folded into lanes 0-1 when i and j
+            // share a 32-colour word, so that no two lanes touch one plane word)
+            const bool same = i && j && ((i >> 5) == (j >> 5));
+            if (c.lane < 4) {
+                uint32_t *P = (c.lane & 1) ? c.s.KP : c.s.RP;
+                const int line = (c.lane & 1) ? cc : r;
+                int dh = 0;
+                if (c.lane < 2) {
+                    if (i) dh += count_step(P, c.cw, line, i, false);
+                    if (same) dh += count_step(P, c.cw, line, j, true);
+                } else if (j && !same) {
+                    dh += count_step(P, c.cw, line, j, true);
+                }
+                if (dh) atomicAdd(&c.s.scal[2], dh);
                 if (c.lane == 0) c.s.S[v] = (uint8_t)j;
             }
             __syncwarp();
+            // counts of colours i and j on the moved row and column, after the move
+            const int Ri = i ? count_of(c.s.RP, c.cw, r, i) : 0, Rj = j ? count_of(c.s.RP, c.cw, r, j) : 0;
+            const int Ki = i ? count_of(c.s.KP, c.cw, cc, i) : 0, Kj = j ? count_of(c.s.KP, c.cw, cc, j) : 0;
             // Conflict status of a mate u can only change if it is the only other
             // member of the line with colour i (count after the move == 1) or with
-            // colour j (count after == 2): skip a line when neither holds.
+            // colour j (count after == 2): lines where neither holds are skipped.
+            const bool need_r = (i && Ri == 1) || (j && Rj == 2);
+            const bool need_c = (i && Ki == 1) || (j && Kj == 2);
+            int rb = 0, re = 0, cb = 0, ce = 0;
+            if (need_r) { rb = __ldg(&I.row_ptr[r]); re = __ldg(&I.row_ptr[r + 1]); }
+            if (need_c) { cb = __ldg(&I.col_ptr[cc]); ce = __ldg(&I.col_ptr[cc + 1]); }
             int dconf = 0;
-            for (int side = 0; side < 2; ++side) {
-                const int line = side ? cc : r;
-                const uint32_t *P = side ? c.s.KP : c.s.RP;
-                const bool need = (i && count_of(P, c.cw, line, i) == 1) || (j && count_of(P, c.cw, line, j) == 2);
-                if (!need) continue;
-                const int32_t *ptr = side ? I.col_ptr : I.row_ptr;
-                const uint16_t *lst = side ? I.col_v : I.row_v;
-                const int qb = __ldg(&ptr[line]), qe = __ldg(&ptr[line + 1]);
-                for (int b0 = qb; b0 < qe; b0 += 32) {
-                    const int qq = b0 + c.lane;
-                    bool want = false;
-                    int u = 0;
-                    if (qq < qe) {
-                        u = __ldg(&lst[qq]);
-                        const int su = c.s.S[u];
-                        if (u != v && su != 0 && (su == i || su == j)) {
-                            const int nc = gamma_of(I, c, u, su) > 0;
-                            const int oc = (c.s.cmask[u >> 5] >> (u & 31)) & 1;
-                            if (nc != oc) {
-                                atomicXor(&c.s.cmask[u >> 5], 1u << (u & 31));
-                                dconf += nc - oc;
-                                want = nc && !((c.s.lmask[u >> 5] >> (u & 31)) & 1u);
-                            }
-                        }
-                    }
-                    list_append(c, want, u, len);
+            const int span_len = max(re - rb, ce - cb);
+            for (int b0 = 0; b0 < span_len; b0 += 32) {
+                const int qr = rb + b0 + c.lane, qc = cb + b0 + c.lane;
+                int ur = -1, uc = -1;
+                if (qr < re) {
+                    const int u = __ldg(&I.row_v[qr]);
+                    const int su = c.s.S[u];
+                    if (u != v && su != 0 && (su == i || su == j)) ur = u | (su << 16);
                 }
+                if (qc < ce) {
+                    const int u = __ldg(&I.col_v[qc]);
+                    const int su = c.s.S[u];
+                    if (u != v && su != 0 && (su == i || su == j)) uc = u | (su << 16);
+                }
+                if (!__any_sync(FULL, ur >= 0 || uc >= 0)) continue;
+                bool wr = false, wc = false;
+                if (ur >= 0) {                           // row-mate: its row count is Ri / Rj
+                    const int u = ur & 0xFFFF, su = ur >> 16;
+                    const int g = (su == i ? Ri : Rj) + count_of(c.s.KP, c.cw, c.rc[u] & 255, su) - 2;
+                    const int nc = g > 0, oc = (c.s.cmask[u >> 5] >> (u & 31)) & 1;
+                    if (nc != oc) {
+                        atomicXor(&c.s.cmask[u >> 5], 1u << (u & 31));
+                        dconf += nc - oc;
+                        wr = nc && !((c.s.lmask[u >> 5] >> (u & 31)) & 1u);
+                    }
+                }
+                if (uc >= 0) {                           // column-mate: its column count is Ki / Kj
+                    const int u = uc & 0xFFFF, su = uc >> 16;
+                    const int g = (su == i ? Ki : Kj) + count_of(c.s.RP, c.cw, c.rc[u] >> 8, su) - 2;
+                    const int nc = g > 0, oc = (c.s.cmask[u >> 5] >> (u & 31)) & 1;
+                    if (nc != oc) {
+                        atomicXor(&c.s.cmask[u >> 5], 1u << (u & 31));
+                        dconf += nc - oc;
+                        wc = nc && !((c.s.lmask[u >> 5] >> (u & 31)) & 1u);
+                    }
+                }
+                list_append(c, wr, ur & 0xFFFF, len);
+                list_append(c, wc, uc & 0xFFFF, len);
             }
             if (c.lane == 0) {
-                const int newc = j ? (int)(gamma_of(I, c, v, j) > 0) : 0;
+                const int newc = j ? (int)(Rj + Kj - 2 > 0) : 0;
                 if (j != 0 && !newc) atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
                 dconf += newc - (i != 0 ? 1 : 0);
             }
             dconf = __reduce_add_sync(FULL, dconf);
             if (c.lane == 0) {
                 const int k = f + nconf + dconf;
-                const int T = L + (a.alpha_num * k) / a.alpha_den;
+                const int T = L + tenure_div(a, a.alpha_num * k);
                 tabu_insert(I, c, G, ck, v, i, trel + (uint32_t)T);
                 c.s.scal[4] = nconf + dconf;
                 c.s.scal[0] = len;
@@ -837,8 +1015,7 @@ __device__ __forceinline__ void repair(const DevInst &I, const Ctx &c)
             const int k = c.s.S[v];
             const uint16_t rc = c.rc[v];
             c.s.S[v] = 0;
-            count_step(c.s.RP, c.cw, rc >> 8, k, false);
-            count_step(c.s.KP, c.cw, rc & 255, k, false);
+            c.s.scal[2] += count_step(c.s.RP, c.cw, rc >> 8, k, false) + count_step(c.s.KP, c.cw, rc & 255, k, false);
         }
         gsync<NW>(c);
     }
@@ -886,6 +1063,7 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         const int L = (int)__shfl_sync(FULL, Lr, q);
         const int rsh = (int)__shfl_sync(FULL, rotr, q);
         const int A = fbest - f;
+        const bool low = c.s.scal[2] == 0;            // every count <= 3
         unsigned long long key = kNoKey;
         int live = 0;
         for (int qq = c.gt; qq < len; qq += 32 * NW) {
@@ -893,7 +1071,10 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
             if (!((c.s.cmask[v >> 5] >> (v & 31)) & 1u)) continue;
             ++live;
             int pairs;
-            const int kv = eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs);
+            bool slow = true;
+            int kv = INT_MAX;
+            if (low) kv = eval_vertex_low<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs, slow);
+            if (slow) kv = eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs);
             st.pairs += pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, 0));
         }
@@ -912,7 +1093,7 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         if (c.wg == 0) {
             const uint16_t rc = c.rc[v];
             const int r = rc >> 8, cc = rc & 255;
-            const int T = L + (a.alpha_num * (f + d)) / a.alpha_den;
+            const int T = L + tenure_div(a, a.alpha_num * (f + d));
             if (c.lane == 0) c.s.scal[5] = 0;
             __syncwarp();
             // row- and column-mates coloured j lose their colour
@@ -944,14 +1125,13 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
                         const int u = ulist[k];
                         const uint16_t rcu = c.rc[u];
                         c.s.S[u] = 0;
-                        count_step(c.s.RP, c.cw, rcu >> 8, j, false);
-                        count_step(c.s.KP, c.cw, rcu & 255, j, false);
+                        c.s.scal[2] += count_step(c.s.RP, c.cw, rcu >> 8, j, false) +
+                                       count_step(c.s.KP, c.cw, rcu & 255, j, false);
                         atomicOr(&c.s.cmask[u >> 5], 1u << (u & 31));
                         tabu_insert(I, c, G, ck, u, j, trel + (uint32_t)T);
                     }
                     c.s.S[v] = (uint8_t)j;
-                    count_step(c.s.RP, c.cw, r, j, true);
-                    count_step(c.s.KP, c.cw, cc, j, true);
+                    c.s.scal[2] += count_step(c.s.RP, c.cw, r, j, true) + count_step(c.s.KP, c.cw, cc, j, true);
                     atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
                 }
                 __syncwarp();

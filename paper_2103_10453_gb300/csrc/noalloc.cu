@@ -87,10 +87,13 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
         return fail(h, PLSE_ENOTSUP,
                     "plse_local_search_noalloc: one walk slot needs %zu bytes of scratch, more than the %zu "
                     "available", table_bytes + 4, kNoAllocScratchBytes - kCounterBytes);
-    LSLaunch L = plan_local_search(h->di, device, count, h->ls_warps);
+    LSLaunch L = plan_local_search(h->di, device, count, h->ls_warps, h->ls_walks);
     if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: local search does not fit");
     if ((size_t)L.slots() > max_slots) {
-        if ((size_t)L.walks > max_slots) L = plan_local_search(h->di, device, count, h->ls_warps, (int)max_slots);
+        if ((size_t)L.walks > max_slots) {
+            const int cap = h->ls_walks > 0 ? std::min(h->ls_walks, (int)max_slots) : (int)max_slots;
+            L = plan_local_search(h->di, device, count, h->ls_warps, cap);
+        }
         L.blocks = (int)std::min<size_t>((size_t)L.blocks, max_slots / (size_t)L.walks);
         if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: no walk slot fits");
     }
@@ -122,6 +125,7 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     a.alpha_num = p.alpha_num;
     a.alpha_den = p.alpha_den;
     a.tenure_rand = p.tenure_rand;
+    a.alpha_recip = h->alpha_recip;
     const int tmax = max_tenure(h);
     a.span1 = (int)(a.iters1 + tmax + 2);
     a.span2 = (int)(a.iters2 + tmax + 2);

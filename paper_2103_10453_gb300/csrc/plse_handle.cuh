@@ -47,6 +47,8 @@ struct plse_instance {
     std::vector<uint16_t> row_v, col_v;
     std::vector<uint4> allow_row, allow_col;
     int ls_warps = 0;                  // warps per walk of the local search (0 = automatic)
+    int ls_walks = 0;                  // cap on concurrent walks per block (0 = fill shared memory)
+    uint32_t alpha_recip = 0;          // reciprocal of alpha_den for the tenure (0: divide)
     plse_params params{};
     void *inst_mem = nullptr;        // one device allocation holding the DevInst arrays
     plse::DevInst di{};
@@ -63,6 +65,7 @@ namespace plse {
 int fail(plse_instance *h, int code, const char *fmt, ...);
 int cuda_fail(plse_instance *h, cudaError_t e, const char *where);
 int max_tenure(const plse_instance *h);
+uint32_t tenure_reciprocal(int alpha_num, int alpha_den, int nv);
 int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
                          int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
                          int64_t *F_out, plse_walk_stats *stats, cudaStream_t st,

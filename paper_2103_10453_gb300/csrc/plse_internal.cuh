@@ -48,6 +48,7 @@ struct LSArgs {
     uint32_t key0, key1;          // Philox key = seed
     int phi2_1, phi2_2;           // 2*phi of phase 1 and phase 2
     int alpha_num, alpha_den, tenure_rand;
+    uint32_t alpha_recip;         // ceil(2^32 / alpha_den) if exact for every x <= alpha_num*|V|, else 0
     int span1, span2;             // clock span reserved per phase (iterations + max tenure + 2)
     int32_t *f_out;
     int64_t *F_out;

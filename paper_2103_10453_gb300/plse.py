@@ -64,7 +64,7 @@ SIGNATURES = {
     "plse_last_error_detail": (C.c_int, [_vp, C.c_char_p, C.c_size_t]),
     "plse_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "plse_sync": (C.c_int, [_vp, _vp]),
-    "plse_set_launch": (C.c_int, [_vp, C.c_int]),
+    "plse_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "plse_default_params": (None, [C.POINTER(Params)]),
     "plse_set_params": (C.c_int, [_vp, C.POINTER(Params)]),
     "plse_get_params": (C.c_int, [_vp, C.POINTER(Params)]),
@@ -178,9 +178,10 @@ class Instance:
         self._check(self.lib.plse_get_params(self.h, C.byref(p)))
         return p
 
-    def set_launch(self, ls_warps: int = 0):
-        """Warps per walk of the local-search kernel (results do not depend on it)."""
-        self._check(self.lib.plse_set_launch(self.h, ls_warps))
+    def set_launch(self, ls_warps: int = 0, ls_walks: int = 0):
+        """Warps per walk and walks per block of the local-search kernel (results
+        do not depend on them)."""
+        self._check(self.lib.plse_set_launch(self.h, ls_warps, ls_walks))
 
     def sync(self, stream=None):
         self._check(self.lib.plse_sync(self.h, _stream(stream)))
