@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--pop", type=int, default=POP)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ls-case", type=float, default=None, metavar="R",
+                    help="small profiling case instead of the benchmark: steady-state phase-1 local "
+                         "search on the n=70 instance with fill ratio R (population --pop, "
+                         "--ls-iters iterations per launch, --steps launches)")
+    ap.add_argument("--ls-iters", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -236,7 +241,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, plse, inputs, seed)
     if rank == 0 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(sample_seconds=20.0)
+        out["cpu_baseline"] = cpu_baseline(sample_seconds=15.0)
     for G in insts:
         G.close()
     if world > 1:
@@ -273,38 +278,58 @@ def run_e2e(args, plse, inputs, seed):
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(per_instance=1, budget_s=20.0):
-    """The CPU oracle as it stands on a bounded sample of the workload: for each
-    instance, one individual is brought to a steady state by an untimed
-    two-phase walk from a random colouring, then one generation's local search
-    (phase 1 with 10|V| iterations, phase 2, repair) of that individual is timed.
+def oracle_sample(budget_s=15.0):
+    """The CPU oracle as it stands on a bounded sample of the workload, in the
+    GA's steady state.  For each of the five instances two individuals A, B are
+    brought to a steady state by an untimed generation of local search from
+    random colourings.  Then, until that instance's share of the budget is
+    spent: the AUX offspring of A with partner B (untimed, cheap) gets one timed
+    generation of local search (phase 1 with 10|V| iterations, phase 2 with
+    2|V|, repair), and the pair becomes (B, result).  Single-threaded.
     Returns (moves, seconds, description)."""
+    import numpy as np
     import oracle
     from paper_2103_10453_gb300 import inputs
     oracle.build()
-    moves, secs = 0, 0.0
+    moves, secs, gens = 0, 0.0, 0
+    share = budget_s / len(RATIOS)
+
+    def generation(I, S, ind, gen):
+        S1, _, st1 = I.tabu_walk(S, ind, gen, 1, 10 * I.nv, 1)
+        S2, _, st2 = I.tabu_walk(S1, ind, gen, 2, 2 * I.nv, 1)
+        S3, _ = I.repair(S2)
+        return S3, st1["moves"] + st2["moves"]
+
     for r in RATIOS:
         I = oracle.Instance(inputs.n70(r))
-        for i in range(per_instance):
-            P = I.init_population(1, 1)
-            S, _, _ = I.tabu_walk(P[0], i, 0, 1, 10 * I.nv, 1)
-            S, _, _ = I.tabu_walk(S, i, 0, 2, 2 * I.nv, 1)
-            S, _ = I.repair(S)
+        P0 = I.init_population(2, 1)
+        A, _ = generation(I, P0[0], 0, 0)
+        B, _ = generation(I, P0[1], 1, 0)
+        t_inst, gen = 0.0, 1
+        while t_inst < share:
+            d = int(I.distances(A, B)[0, 0])
+            if d == 0:                      # identical parents: restart B from random
+                B, _ = generation(I, I.init_population(1, 100 + gen)[0], 1, gen)
+                gen += 1
+                continue
+            pair = np.stack([A, B])
+            O = I.crossover(pair, [1, 0], [[0, d], [d, 0]], gen, 1)[0]
             t0 = time.perf_counter()
-            S1, _, st1 = I.tabu_walk(S, i, 1, 1, 10 * I.nv, 1)
-            S2, _, st2 = I.tabu_walk(S1, i, 1, 2, 2 * I.nv, 1)
-            I.repair(S2)
-            secs += time.perf_counter() - t0
-            moves += st1["moves"] + st2["moves"]
-        if secs > budget_s:
-            break
-    desc = ("one steady-state generation of local search (phase 1 10|V| + phase 2 2|V| + repair) "
-            "for %d individual(s) of each n=70 instance, single-threaded C oracle" % per_instance)
+            S, m = generation(I, O, 0, gen)
+            t_inst += time.perf_counter() - t0
+            moves += m
+            A, B = B, S
+            gen += 1
+            gens += 1
+        secs += t_inst
+    desc = ("%d steady-state generations of local search (phase 1 10|V| + phase 2 2|V| + repair) of "
+            "one AUX offspring each, spread over the five n=70 instances, single-threaded C oracle, "
+            "%.1f s timed" % (gens, secs))
     return moves, secs, desc
 
 
-def cpu_baseline(sample_seconds=20.0):
-    moves, secs, desc = oracle_sample(1, sample_seconds)
+def cpu_baseline(sample_seconds=15.0):
+    moves, secs, desc = oracle_sample(sample_seconds)
     return {"value": round(moves / secs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": desc, "seconds": round(secs, 2)}
 
@@ -316,9 +341,9 @@ def run_reference(args):
     vals, total_m, total_s = [], 0, 0.0
     desc = ""
     for _ in range(args.warmup):
-        oracle_sample(1, 5.0)
+        oracle_sample(2.0)
     for _ in range(args.steps):
-        m, s, desc = oracle_sample(1, 10.0)
+        m, s, desc = oracle_sample(10.0)
         vals.append(m / s)
         total_m += m
         total_s += s
@@ -336,9 +361,46 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_ls_case(args):
+    """One instance, one population brought to a steady state by an untimed
+    two-phase walk from random colourings, then --steps phase-1 launches of
+    --ls-iters iterations, each timed with CUDA events on the launching stream.
+    Prints one JSON line; meant as the small case for kernel profiles."""
+    import torch
+    from paper_2103_10453_gb300 import inputs, plse
+    G = plse.Instance(inputs.n70(args.ls_case))
+    pop = args.pop
+    P = torch.empty((pop, G.nv), dtype=torch.uint8, device="cuda")
+    Q = torch.empty_like(P)
+    st = torch.zeros((pop, 7), dtype=torch.int64, device="cuda")
+    G.init_population(pop, 1, P)
+    G.local_search(P, Q, pop, 0, 0, 10 * G.nv, 1, plse.LS_PHASE1 | plse.LS_PHASE2 | plse.LS_REPAIR,
+                   stats=st)
+    G.sync()
+    runs = []
+    for k in range(args.steps):
+        src, dst = (Q, P) if k % 2 == 0 else (P, Q)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.local_search(src, dst, pop, 0, 1 + k, args.ls_iters, 1, plse.LS_PHASE1, stats=st)
+        e1.record()
+        G.sync()
+        s = st.sum(0).tolist()
+        ms = e0.elapsed_time(e1)
+        runs.append({"ms": round(ms, 3), "moves_per_s": round(s[1] / ms * 1e3, 1),
+                     "cand_per_iter": round(s[2] / max(s[0], 1), 2),
+                     "pairs_per_iter": round(s[3] / max(s[0], 1), 2),
+                     "bytes_alg": walk_bytes(dict(zip(["iterations", "moves", "cand", "pairs", "deg"], s)))})
+    print(json.dumps({"case": "ls_steady", "n": 70, "r": args.ls_case, "nv": G.nv, "population": pop,
+                      "iters": args.ls_iters, "runs": runs}), flush=True)
+    G.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.ls_case is not None:
+        run_ls_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
