@@ -48,6 +48,18 @@ def parse():
                          "search on the n=70 instance with fill ratio R (population --pop, "
                          "--ls-iters iterations per launch, --steps launches)")
     ap.add_argument("--ls-iters", type=int, default=3000)
+    ap.add_argument("--batch", action="store_true",
+                    help="batching case instead of the benchmark: 64 uneven instances solved one "
+                         "by one with plse_solve, then together with plse_solve_batch")
+    ap.add_argument("--batch-pop", type=int, default=1024)
+    ap.add_argument("--generations", type=int, default=10,
+                    help="generations per job of --batch and --serve")
+    ap.add_argument("--inflight", type=int, default=16)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving case instead of the benchmark: Poisson arrivals into the "
+                         "library's request server, latency percentiles")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -396,10 +408,98 @@ def run_ls_case(args):
     G.close()
 
 
+def run_batch_case(args):
+    """64 uneven instances (n in {20..70}, r ~ U[0.3, 0.8], cyclic-delete or
+    random insertion by a coin, seeds 4000+k), population --batch-pop,
+    --generations generations, phase-1 iterations 10|V|, optimality stop on.
+    Wall clock of 64 sequential plse_solve calls against one plse_solve_batch
+    call; every job's score, grid and walk counters must be identical."""
+    import numpy as np
+    import torch
+    from paper_2103_10453_gb300 import inputs, plse
+    grids = inputs.batch_mix(64)
+    insts = [plse.Instance(g) for g in grids]
+    jobs = [(args.batch_pop, args.generations, 10 * G.nv, 1) for G in insts]
+    insts[0].solve(*jobs[0])                       # warm-up: module load, first allocations
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [G.solve(*j, with_stats=True) for G, j in zip(insts, jobs)]
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bat, rc = plse.solve_batch(insts, jobs, max_inflight=args.inflight)
+    t_bat = time.perf_counter() - t0
+    same = rc == 0 and all(a["score"] == b["score"] and np.array_equal(a["best_grid"], b["best_grid"])
+                           and a["walks"] == b["walks"] for a, b in zip(seq, bat))
+    moves = sum(r["walks"]["moves"] for r in bat)
+    print(json.dumps({"case": "batch", "jobs": len(jobs), "population": args.batch_pop,
+                      "generations": args.generations, "max_inflight": args.inflight,
+                      "sequential_s": round(t_seq, 3), "batched_s": round(t_bat, 3),
+                      "speedup": round(t_seq / t_bat, 3), "identical": bool(same),
+                      "moves": moves, "batched_moves_per_s": round(moves / t_bat, 1),
+                      "sequential_moves_per_s": round(moves / t_seq, 1),
+                      "solved_to_bound": sum(1 for G, r in zip(insts, bat) if r["score"] == G.ub)}),
+          flush=True)
+    for G in insts:
+        G.close()
+
+
+def serve_pop(grid):
+    """Population of a serving request, fixed by its size alone: 2^16 / (empty
+    cells), rounded down to a power of two, within [32, 512]."""
+    empty = max(int((grid == 0).sum()), 1)
+    p = 32
+    while p * 2 <= 512 and p * 2 * empty <= (1 << 16):
+        p *= 2
+    return p
+
+
+def run_serve_case(args):
+    """--requests requests with Poisson arrivals at --rate per second into one
+    plse_server (max_inflight --inflight): a quarter LSC-style cyclic-delete
+    requests with n in [60, 100], the rest random insertion with n uniform over
+    {10..100}, r ~ U[0.3, 0.8], seeds 5000+k; --generations generations with the
+    optimality stop, phase-1 iterations 10 x empty cells, population by size.
+    Reports time-to-result percentiles (arrival to completion) and solves/s."""
+    import numpy as np
+    from paper_2103_10453_gb300 import inputs, plse
+    grids = inputs.serve_mix(args.requests)
+    arrivals = inputs.poisson_arrivals(args.requests, args.rate)
+    srv = plse.Server(max_inflight=args.inflight, max_queue=args.requests)
+    # warm-up request (module load, first allocations), not counted
+    w = srv.submit(inputs.tiny_n10(), 32, 2, 100, 1)
+    srv.poll(w, wait_ms=-1)
+    tickets = []
+    t0 = time.perf_counter()
+    for g, ta in zip(grids, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        empty = int((g == 0).sum())
+        tickets.append(srv.submit(g, serve_pop(g), args.generations, 10 * empty, 1))
+    res = [srv.poll(t, wait_ms=-1) for t in tickets]
+    t_all = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([r["ms_wall"] for r in res])
+    ok = sum(1 for r in res if r["status"] == 0)
+    print(json.dumps({"case": "serve", "requests": args.requests, "rate_per_s": args.rate,
+                      "max_inflight": args.inflight, "generations": args.generations,
+                      "ok": ok, "wall_s": round(t_all, 3), "solves_per_s": round(ok / t_all, 3),
+                      "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
+                                     "p90": round(float(np.percentile(lat, 90)), 1),
+                                     "p99": round(float(np.percentile(lat, 99)), 1),
+                                     "max": round(float(lat.max()), 1)},
+                      "queue_ms_p50": round(float(np.percentile([r["ms_queue"] for r in res], 50)), 1),
+                      "moves": sum(r["walks"]["moves"] for r in res)}), flush=True)
+
+
 def main():
     args = parse()
     if args.ls_case is not None:
         run_ls_case(args)
+    elif args.batch:
+        run_batch_case(args)
+    elif args.serve:
+        run_serve_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

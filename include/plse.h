@@ -37,10 +37,11 @@ extern "C" {
 #define PLSE_EINVAL     -1   /* invalid argument or invalid grid               */
 #define PLSE_ENOMEM     -2   /* host or device allocation failed               */
 #define PLSE_ECUDA      -3   /* CUDA runtime error                             */
-#define PLSE_EBUSY      -4   /* admission refused: not enough device memory    */
-#define PLSE_ECANCELLED -5   /* cancelled through plse_cancel                  */
+#define PLSE_EBUSY      -4   /* admission refused (request queue full)         */
+#define PLSE_ECANCELLED -5   /* cancelled through plse_server_cancel           */
 #define PLSE_ENOTSUP    -6   /* parameter combination not supported            */
 #define PLSE_ECHECK     -7   /* a device-side bound check failed               */
+#define PLSE_PENDING     1   /* plse_server_poll: the request is not complete  */
 
 typedef struct plse_instance *plse_handle;
 
@@ -144,12 +145,85 @@ int  plse_solve_ex(plse_handle h, int pop, int generations, int64_t iters, uint6
  * stopped at the bound or used its generations); plse_run_result copies the
  * best grid, score and statistics of the run so far.  plse_solve is
  * begin + step + result.  One run per handle at a time; a new begin discards
- * the previous run. */
+ * the previous run.  Every call of a run takes the stream given to
+ * plse_run_begin (plse_run_step returns PLSE_EINVAL for another one). */
 int  plse_run_begin(plse_handle h, int pop, int max_generations, int64_t iters, uint64_t seed,
                     void *stream);
 int  plse_run_step(plse_handle h, int generations, void *stream, int *done);
 int  plse_run_result(plse_handle h, void *stream, int8_t *best_grid, int *best_score,
                      plse_solve_stats *stats, int32_t *trace);
+
+/* Non-blocking form of plse_run_step, for callers that drive several runs from
+ * one host thread (each run on its own stream, so their kernels overlap).
+ * plse_run_issue enqueues the run's next generation on `stream` (which must be
+ * the stream given to plse_run_begin; PLSE_EINVAL otherwise) without waiting
+ * for anything, unless the run has finished, has enqueued all its generations
+ * or already has two generations in flight; *issued (may be NULL) says whether
+ * it did.  plse_run_query never waits: it takes note of completed generations
+ * and reports *done = 1 once the run has finished (bound reached or
+ * generations used) and nothing of it is in flight, *generations = completed
+ * generations and *in_flight = enqueued but not yet completed (each may be
+ * NULL).  A generation enqueued before the host saw the stop returns at entry
+ * in every kernel, so results equal those of plse_run_step.  plse_run_result
+ * and plse_destroy wait for the generations in flight. */
+int  plse_run_issue(plse_handle h, void *stream, int *issued);
+int  plse_run_query(plse_handle h, int *done, int *generations, int *in_flight);
+
+/* ---- many jobs at once ------------------------------------------------------
+ * A job is one plse_solve: population, generations, phase-1 iterations, seed. */
+typedef struct {
+    int32_t  pop;             /* 2..65535                                       */
+    int32_t  generations;     /* 0..65534                                       */
+    int64_t  iters;           /* phase-1 tabu iterations, 0..2^30               */
+    uint64_t seed;
+} plse_job;
+
+typedef struct {
+    int32_t status;           /* PLSE_OK, or the job's own negative code        */
+    int32_t best_score;       /* as plse_solve                                  */
+    plse_solve_stats stats;   /* as plse_solve_ex                               */
+    double  ms_queue;         /* host wall time from submission to the start    */
+    double  ms_wall;          /* host wall time from submission to completion   */
+} plse_result;
+
+/* plse_solve_batch -- runs job i on handle hs[i] (with that handle's
+ * parameters), up to `max_inflight` jobs at a time (0 = 16), each on its own
+ * stream, with their kernels overlapping on the current device; jobs naming the
+ * same handle run one after another.  best_grids (may be NULL, entries may be
+ * NULL): host int8 [n_i*n_i] outputs as plse_solve.  results: host [count].
+ * Every job's result equals that of plse_solve with the same arguments.
+ * Blocks until every job is done; returns the first job error (in index order)
+ * or PLSE_OK; results[i].status holds each job's own code. */
+int  plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count, int max_inflight,
+                      int8_t *const *best_grids, plse_result *results);
+
+/* Request server: a host thread of the library that admits submitted requests
+ * (grid + job + parameters) into `max_inflight` concurrent runs on the device
+ * that is current at plse_server_create, in arrival order, and keeps each
+ * result until it is polled.  Per-request results are identical to plse_solve
+ * of the same request alone (the job's size never depends on load).
+ *   submit: copies `grid` (n*n) and `params` (NULL = defaults); returns a
+ *     ticket, or PLSE_EBUSY when `max_queue` requests already wait (admission
+ *     refused; nothing is queued), PLSE_EINVAL for a malformed request (grids
+ *     are validated at admission: a bad one completes with PLSE_EINVAL).
+ *   poll: waits up to wait_ms (0 = not at all, -1 = until done); PLSE_PENDING
+ *     if the request is not complete, else PLSE_OK with *out and best_grid
+ *     (host n*n, may be NULL) written and the ticket released; PLSE_EINVAL for
+ *     an unknown or released ticket.
+ *   cancel: a waiting request completes with PLSE_ECANCELLED without running;
+ *     a running one stops enqueueing generations and completes with
+ *     PLSE_ECANCELLED and its best so far once its generations in flight end.
+ *   pending: requests waiting for admission and results not yet polled.
+ *   destroy: cancels what is waiting or running, joins the threads, frees all. */
+typedef struct plse_server_s *plse_server;
+int  plse_server_create(int max_inflight, int max_queue, plse_server *out);
+int  plse_server_submit(plse_server s, int n, const int8_t *grid, const plse_job *job,
+                        const plse_params *params, int64_t *ticket);
+int  plse_server_poll(plse_server s, int64_t ticket, int wait_ms, int8_t *best_grid,
+                      plse_result *out);
+int  plse_server_cancel(plse_server s, int64_t ticket);
+int  plse_server_pending(plse_server s, int *queued, int *completed);
+void plse_server_destroy(plse_server s);
 
 /* ---- step entry points (device buffers, asynchronous on `stream`) ---------
  * plse_init_population -- Sec. 3.2: P[i][v] uniform over D(v)\{0}, individual

@@ -205,32 +205,35 @@ int max_tenure(const plse_instance *h)
 }
 
 template <typename T>
-static int grow(plse_instance *h, T *&ptr, size_t &cap, size_t need, bool zero)
+static int grow(plse_instance *h, T *&ptr, size_t &cap, size_t need, bool zero, cudaStream_t st)
 {
     if (need <= cap) return PLSE_OK;
     if (ptr) { cudaFree(ptr); ptr = nullptr; cap = 0; }
     cudaError_t e = cudaMalloc(&ptr, need * sizeof(T));
     if (e != cudaSuccess) { ptr = nullptr; return fail(h, PLSE_ENOMEM, "workspace: %s", cudaGetErrorString(e)); }
     if (zero) {
-        e = cudaMemset(ptr, 0, need * sizeof(T));
+        e = cudaMemsetAsync(ptr, 0, need * sizeof(T), st);   // in order with the launch that needs it
         if (e != cudaSuccess) return cuda_fail(h, e, "workspace clear");
     }
     cap = need;
     return PLSE_OK;
 }
 
-int ensure_ls_workspace(plse_instance *h, int slots)
+int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
 {
     Workspace &ws = h->ws;
-    int rc = grow(h, ws.G, ws.G_cap, (size_t)slots * h->di.nv * h->di.n1p, true);
+    int rc = grow(h, ws.G, ws.G_cap, (size_t)slots * h->di.nv * h->di.n1p, true, st);
     if (rc) return rc;
     if ((size_t)slots > ws.clock_cap) {
         // the slot clocks index the same slots as G: reset both together
-        if (ws.G) cudaMemset(ws.G, 0, ws.G_cap * sizeof(uint32_t));
+        if (ws.G && cudaMemsetAsync(ws.G, 0, ws.G_cap * sizeof(uint32_t), st) != cudaSuccess)
+            return fail(h, PLSE_ECUDA, "workspace clear");
     }
-    rc = grow(h, ws.slot_clock, ws.clock_cap, (size_t)slots, true);
+    rc = grow(h, ws.TC, ws.TC_cap, (size_t)slots * h->di.nv, false, st);   // reset by every phase
     if (rc) return rc;
-    return grow(h, ws.counters, ws.counters_cap, 8, true);
+    rc = grow(h, ws.slot_clock, ws.clock_cap, (size_t)slots, true, st);
+    if (rc) return rc;
+    return grow(h, ws.counters, ws.counters_cap, 8, true, st);
 }
 
 int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
@@ -264,9 +267,10 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.skip = skip;
     LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_warps, h->ls_walks);
     if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "local search does not fit on this device");
-    int rc = ensure_ls_workspace(h, L.slots());
+    int rc = ensure_ls_workspace(h, L.slots(), st);
     if (rc) return rc;
     a.G = h->ws.G;
+    a.TC = h->ws.TC;
     a.slot_clock = h->ws.slot_clock;
     a.work_counter = h->ws.counters;
     a.error_flag = h->ws.counters + 1;
@@ -339,10 +343,12 @@ int plse_create(int n, const int8_t *grid, plse_handle *out)
 void plse_destroy(plse_handle h)
 {
     if (!h) return;
+    run_drain(h);            // nothing of the handle may still run on the device
     release_solver(h);
     if (h->inst_mem) cudaFree(h->inst_mem);
     Workspace &ws = h->ws;
     if (ws.G) cudaFree(ws.G);
+    if (ws.TC) cudaFree(ws.TC);
     if (ws.slot_clock) cudaFree(ws.slot_clock);
     if (ws.counters) cudaFree(ws.counters);
     delete h;

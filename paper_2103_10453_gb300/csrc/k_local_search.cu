@@ -81,8 +81,7 @@ __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
     p.off_lmask = o;  o += 4 * (size_t)I.nw;
     p.off_list = align16(o);
     o = align16(p.off_list + 2 * (size_t)I.nv);
-    p.off_tc = o;     o += 8 * (size_t)I.nv;
-    p.off_red = align16(o);
+    p.off_red = o;
     o = p.off_red + 8 * 2 * (size_t)warps + 4 * 2 * (size_t)warps + 4 * 16;
     p.slot = align16(o);
     return p;
@@ -95,7 +94,8 @@ struct Slot {
     uint32_t *cmask;            // candidate bitmask [nw]
     uint32_t *lmask;            // vertices present in the candidate list [nw]
     uint16_t *list;             // candidate list (may hold stale entries) [nv]
-    uint2 *tc;                  // tabu cache [nv]: x = e0 | e1 << 16, y = c0 | c1 << 8 | emax << 16
+    uint2 *tc;                  // tabu cache [nv] in global memory (L1-resident for the candidates):
+                                // x = e0 | e1 << 16, y = c0 | c1 << 8 | emax << 16
     unsigned long long *red;    // [2][NW] best key per warp (double-buffered)
     int *red_cnt;               // [2][NW] live candidates seen per warp
     int *scal;                  // [16]: 0 list length, 4 |C(S)|, 5..6 PartialCol, 7 walk id, 8.. reductions
@@ -137,7 +137,7 @@ __device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I)
     c.s.cmask = reinterpret_cast<uint32_t *>(sb + p.off_cmask);
     c.s.lmask = reinterpret_cast<uint32_t *>(sb + p.off_lmask);
     c.s.list = reinterpret_cast<uint16_t *>(sb + p.off_list);
-    c.s.tc = reinterpret_cast<uint2 *>(sb + p.off_tc);
+    c.s.tc = nullptr;           // set once the walk slot is known
     c.s.red = reinterpret_cast<unsigned long long *>(sb + p.off_red);
     c.s.red_cnt = reinterpret_cast<int *>(sb + p.off_red + 16 * NW);
     c.s.scal = c.s.red_cnt + 2 * NW;
@@ -1173,10 +1173,11 @@ __global__ void __launch_bounds__(256, NWC >= 3 ? 1 : 2) local_search_kernel(con
     for (int r = threadIdx.x; r < 2 * I.n; r += blockDim.x) allow_s[r] = r < I.n ? I.allow_row[r] : I.allow_col[r - I.n];
     __syncthreads();
 
-    const Ctx c = make_ctx<NW>(smem, I);
+    Ctx c = make_ctx<NW>(smem, I);
     if (c.g >= walks) return;
     const int slot = blockIdx.x * walks + c.g;
     uint32_t *G = a.G + (size_t)slot * I.nv * I.n1p;
+    c.s.tc = a.TC + (size_t)slot * I.nv;
 
     for (;;) {
         if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);

@@ -16,6 +16,8 @@ struct SolverState;   // generation-loop buffers (solve.cu)
 struct Workspace {
     uint32_t *G = nullptr;          // evicted tabu expiries, one table per walk slot
     size_t G_cap = 0;
+    uint2 *TC = nullptr;            // two-entry tabu caches, one array per walk slot
+    size_t TC_cap = 0;
     uint32_t *slot_clock = nullptr; // per-slot clock
     size_t clock_cap = 0;
     int *counters = nullptr;        // [0] walk counter, [1] error flag, [2..] spare
@@ -26,6 +28,8 @@ struct Workspace {
 struct Session {
     int active = 0, finished = 0;
     int pop = 0, max_gens = 0, gen = 0, cur = 0;
+    int issued = 0;     // generations enqueued on the device
+    int polled = 0;     // enqueued generations whose completion the host has seen
     int64_t iters = 0;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
@@ -71,4 +75,16 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
                          int64_t *F_out, plse_walk_stats *stats, cudaStream_t st,
                          const int *skip = nullptr);
 void release_solver(plse_instance *h);
+
+// resumable run of Alg. 2 (solve.cu).  run_issue enqueues one more generation
+// when fewer than two are in flight (never waits); run_poll consumes completed
+// generations (wait = block until every enqueued one completed); run_drain is
+// run_poll(wait) when anything is in flight.
+int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uint64_t seed, cudaStream_t st);
+int run_issue(plse_instance *h, int *issued);
+int run_poll(plse_instance *h, bool wait);
+int run_drain(plse_instance *h);
+int run_step(plse_instance *h, int generations, cudaStream_t st, int *done_out);
+int run_result(plse_instance *h, cudaStream_t st, int8_t *best_grid, int *best_score, plse_solve_stats *stats,
+               int32_t *trace_out);
 }  // namespace plse

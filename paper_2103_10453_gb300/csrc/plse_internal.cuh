@@ -55,6 +55,7 @@ struct LSArgs {
     plse_walk_stats *stats;
     // scratch (global memory owned by the handle's workspace)
     uint32_t *G;                  // [slots][nv * n1p] evicted tabu expiries (absolute clock)
+    uint2 *TC;                    // [slots][nv] two-entry tabu caches (relative clock)
     uint32_t *slot_clock;         // [slots] next free clock value of each slot
     int *work_counter;            // dynamic walk scheduler, zeroed before launch
     int *error_flag;              // nonzero after a failed device bound check
@@ -74,7 +75,7 @@ struct LSLaunch {
 struct SmemPlan {
     size_t inst;       // vertex coordinates and allowed-colour masks
     size_t slot;       // one walk: colouring, count planes, candidate set, tabu cache, scalars
-    size_t off_S, off_RP, off_KP, off_cmask, off_lmask, off_list, off_tc, off_red;   // within a slot
+    size_t off_S, off_RP, off_KP, off_cmask, off_lmask, off_list, off_red;   // within a slot
     size_t total(int walks) const { return inst + slot * (size_t)walks; }
 };
 

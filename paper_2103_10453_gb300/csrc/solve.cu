@@ -10,6 +10,7 @@
 //   matching + AUX -> next S^O                        (Alg. 5)
 // Once the bound is reached every later kernel of the run returns at entry, so
 // the host only reads the 4-byte flag once per generation.
+#include <algorithm>
 #include <climits>
 #include <cstring>
 
@@ -17,6 +18,10 @@
 #include "plse_pop.cuh"
 
 namespace plse {
+
+// generations of one run that may be enqueued before the host has seen the
+// first of them complete
+constexpr int kGenDepth = 2;
 
 struct Ctrl {
     int fstar;      // f(S*)
@@ -43,6 +48,9 @@ struct SolverState {
     uint8_t *Sstar = nullptr;
     int32_t *trace = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // per in-flight generation: local search begin / end, flag copied to the host
+    cudaEvent_t gev[kGenDepth][3] = {};
+    int *hflag = nullptr;                    // pinned host [kGenDepth][2]: f*, done
 };
 
 namespace {
@@ -225,6 +233,9 @@ void release_solver(plse_instance *h)
     cudaFree(s->wstats); cudaFree(s->ctrl); cudaFree(s->Sstar); cudaFree(s->trace);
     free_pop_scratch(s->ps);
     for (auto &ev : s->ev) if (ev) cudaEventDestroy(ev);
+    for (auto &g : s->gev)
+        for (auto &ev : g) if (ev) cudaEventDestroy(ev);
+    if (s->hflag) cudaFreeHost(s->hflag);
     delete s;
     h->solver = nullptr;
     // step scratch
@@ -251,6 +262,9 @@ static int ensure_solver(plse_instance *h, int p, int gens)
         cudaFree(old->trace);
         free_pop_scratch(old->ps);
         for (auto &ev : old->ev) if (ev) cudaEventDestroy(ev);
+        for (auto &g : old->gev)
+            for (auto &ev : g) if (ev) cudaEventDestroy(ev);
+        if (old->hflag) cudaFreeHost(old->hflag);
         delete old;
         h->solver = nullptr;
     }
@@ -273,6 +287,14 @@ static int ensure_solver(plse_instance *h, int p, int gens)
     if ((rc = ensure_pop_scratch(h, s->ps, p))) return rc;
     for (auto &ev : s->ev)
         if (cudaEventCreate(&ev) != cudaSuccess) return fail(h, PLSE_ECUDA, "event create");
+    for (auto &g : s->gev)
+        for (auto &ev : g)
+            if (cudaEventCreate(&ev) != cudaSuccess) return fail(h, PLSE_ECUDA, "event create");
+    if (cudaHostAlloc(reinterpret_cast<void **>(&s->hflag), sizeof(int) * 2 * kGenDepth, cudaHostAllocDefault) !=
+        cudaSuccess) {
+        s->hflag = nullptr;
+        return fail(h, PLSE_ENOMEM, "pinned host allocation");
+    }
     s->cap_p = p;
     s->cap_gens = gens;
     s->tested_cap = cap;
@@ -298,6 +320,8 @@ int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uin
         iters > (1ll << 30))
         return fail(h, PLSE_EINVAL, "plse_run_begin: invalid argument");
     Session &se = h->session;
+    int rc = run_drain(h);
+    if (rc) return rc;
     se = Session();
     se.pop = pop;
     se.iters = iters;
@@ -309,7 +333,7 @@ int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uin
     const int ftarget = h->l == 1 ? 1 : 0;
     se.finished = (nv == 0 || nv <= ftarget || max_generations == 0);
     if (se.finished) return PLSE_OK;
-    int rc = ensure_solver(h, pop, max_generations);
+    rc = ensure_solver(h, pop, max_generations);
     if (rc) return rc;
     SolverState *s = h->solver;
     const DevInst &I = h->di;
@@ -333,55 +357,114 @@ int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uin
     return PLSE_OK;
 }
 
+// Enqueues generation se.issued of the run on its stream without waiting for
+// anything: local search, best update, an 8-byte copy of (f*, done) to pinned
+// host memory, then Alg. 4, gather, matching and crossover.  If the bound is
+// reached in this or an earlier generation, every later kernel returns at
+// entry, so generations enqueued past the stop leave no trace in the results.
+static int issue_generation(plse_instance *h)
+{
+    Session &se = h->session;
+    SolverState *s = h->solver;
+    const cudaStream_t st = se.stream;
+    const DevInst &I = h->di;
+    const plse_params &prm = h->params;
+    const int nv = h->nv;
+    const int ftarget = h->l == 1 ? 1 : 0;
+    const int p = se.pop, cap = prm.tested_cap, g = se.issued, cur = se.cur, nxt = cur ^ 1;
+    const int slot = g % kGenDepth;
+    const size_t PV = (size_t)p * nv, stride = (size_t)I.nw * I.nb;
+    const int *skip = prm.stop_at_bound ? &s->ctrl->done : nullptr;
+    const int flags = prm.mode == PLSE_MODE_PARTIALCOL ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
+                                                       : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
+    uint8_t *Pp = s->Pall[cur] + PV;
+    CK(cudaEventRecord(s->gev[slot][0], st));
+    int rc = enqueue_local_search(h, s->SO, Pp, p, 0, g, se.iters, se.seed, flags, s->fprime, nullptr,
+                                  s->wstats, st, skip);
+    if (rc) return rc;
+    CK(cudaEventRecord(s->gev[slot][1], st));
+    best_kernel<<<1, 1024, 0, st>>>(p, nv, ftarget, g, prm.stop_at_bound, s->fprime, Pp, s->wstats,
+                                    s->e[cur] + p, s->ctrl, s->Sstar, s->trace);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(s->hflag + 2 * slot, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(s->gev[slot][2], st));
+    CK(launch_planes(I, Pp, p, s->planes[cur] + (size_t)p * stride, st));
+    CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st));
+    gather_kernel<<<(p * 32 + 255) / 256, 256, 0, st>>>(
+        I, p, g, s->sel, s->Pall[cur], s->planes[cur], s->e[cur], s->uid[cur], s->tested[cur], s->tcount[cur],
+        cap, s->Pall[nxt], s->planes[nxt], s->e[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], skip);
+    CK(cudaGetLastError());
+    CK(launch_matching(I, p, s->planes[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], cap,
+                       prm.matching == PLSE_MATCH_RANDOM, g, se.seed, s->partner, s->dist, skip, st));
+    CK(launch_crossover(I, p, s->Pall[nxt], s->partner, s->dist, g, se.seed, prm.beta,
+                        prm.crossover == PLSE_XOVER_UX, s->SO, skip, st));
+    se.launches += 3 + pop_update_launches(p) + 3;
+    se.cur = nxt;
+    se.issued = g + 1;
+    return PLSE_OK;
+}
+
+int run_issue(plse_instance *h, int *issued)
+{
+    Session &se = h->session;
+    if (issued) *issued = 0;
+    if (!se.active) return fail(h, PLSE_EINVAL, "plse_run_issue: no run in progress");
+    if (se.finished || se.issued >= se.max_gens || se.issued - se.polled >= kGenDepth) return PLSE_OK;
+    const int rc = issue_generation(h);
+    if (!rc && issued) *issued = 1;
+    return rc;
+}
+
+int run_poll(plse_instance *h, bool wait)
+{
+    Session &se = h->session;
+    SolverState *s = h->solver;
+    while (se.polled < se.issued) {
+        const int slot = se.polled % kGenDepth;
+        if (wait) {
+            CK(cudaEventSynchronize(s->gev[slot][2]));
+        } else {
+            const cudaError_t q = cudaEventQuery(s->gev[slot][2]);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) return cuda_fail(h, q, "plse_run_query");
+        }
+        ++se.polled;
+        if (se.finished) continue;   // enqueued past the stop: skipped on the device
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, s->gev[slot][0], s->gev[slot][1]));
+        se.ms_ls += ms;
+        se.gen += 1;
+        if ((h->params.stop_at_bound && s->hflag[2 * slot + 1]) || se.gen >= se.max_gens) se.finished = 1;
+    }
+    if (se.gen >= se.max_gens) se.finished = 1;
+    return PLSE_OK;
+}
+
+int run_drain(plse_instance *h)
+{
+    Session &se = h->session;
+    if (!se.active || se.polled >= se.issued) return PLSE_OK;
+    return run_poll(h, true);
+}
+
 int run_step(plse_instance *h, int generations, cudaStream_t st, int *done_out)
 {
     Session &se = h->session;
     if (!se.active) return fail(h, PLSE_EINVAL, "plse_run_step: no run in progress");
     if (generations < 0) return fail(h, PLSE_EINVAL, "plse_run_step: invalid argument");
-    const DevInst &I = h->di;
-    const plse_params &prm = h->params;
-    const int nv = h->nv;
-    const int ftarget = h->l == 1 ? 1 : 0;
-    for (int k = 0; k < generations && !se.finished; ++k) {
-        if (se.gen >= se.max_gens) { se.finished = 1; break; }
-        SolverState *s = h->solver;
-        const int p = se.pop, cap = prm.tested_cap, g = se.gen, cur = se.cur, nxt = cur ^ 1;
-        const size_t PV = (size_t)p * nv, stride = (size_t)I.nw * I.nb;
-        const int *skip = prm.stop_at_bound ? &s->ctrl->done : nullptr;
-        const int flags = prm.mode == PLSE_MODE_PARTIALCOL ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
-                                                           : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
-        uint8_t *Pp = s->Pall[cur] + PV;
-        CK(cudaEventRecord(s->ev[1], st));
-        int rc = enqueue_local_search(h, s->SO, Pp, p, 0, g, se.iters, se.seed, flags, s->fprime, nullptr,
-                                      s->wstats, st, skip);
-        if (rc) return rc;
-        CK(cudaEventRecord(s->ev[2], st));
-        best_kernel<<<1, 1024, 0, st>>>(p, nv, ftarget, g, prm.stop_at_bound, s->fprime, Pp, s->wstats,
-                                        s->e[cur] + p, s->ctrl, s->Sstar, s->trace);
-        CK(cudaGetLastError());
-        se.launches += 2;
-        // the stop test needs f* on the host: one 8-byte read per generation
-        int hc[2];
-        CK(cudaMemcpyAsync(hc, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, s->ev[1], s->ev[2]));
-        se.ms_ls += ms;
-        se.gen = g + 1;
-        if (prm.stop_at_bound && hc[1]) { se.finished = 1; break; }
-        CK(launch_planes(I, Pp, p, s->planes[cur] + (size_t)p * stride, st));
-        CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st));
-        gather_kernel<<<(p * 32 + 255) / 256, 256, 0, st>>>(
-            I, p, g, s->sel, s->Pall[cur], s->planes[cur], s->e[cur], s->uid[cur], s->tested[cur], s->tcount[cur],
-            cap, s->Pall[nxt], s->planes[nxt], s->e[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], skip);
-        CK(cudaGetLastError());
-        CK(launch_matching(I, p, s->planes[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], cap,
-                           prm.matching == PLSE_MATCH_RANDOM, g, se.seed, s->partner, s->dist, skip, st));
-        CK(launch_crossover(I, p, s->Pall[nxt], s->partner, s->dist, g, se.seed, prm.beta,
-                            prm.crossover == PLSE_XOVER_UX, s->SO, skip, st));
-        se.launches += 1 + pop_update_launches(p) + 3;
-        se.cur = nxt;
+    if (st != se.stream) return fail(h, PLSE_EINVAL, "plse_run_step: not the stream of plse_run_begin");
+    int rc = run_poll(h, false);
+    if (rc) return rc;
+    const long long target = std::min<long long>((long long)se.issued + generations, se.max_gens);
+    while (!se.finished && se.issued < target) {
+        if (se.issued - se.polled < kGenDepth) {
+            if ((rc = issue_generation(h))) return rc;
+        } else if ((rc = run_poll(h, true))) {
+            return rc;
+        }
     }
+    // blocking call: everything it enqueued has completed when it returns
+    if ((rc = run_drain(h))) return rc;
     if (done_out) *done_out = se.finished;
     return PLSE_OK;
 }
@@ -391,6 +474,8 @@ int run_result(plse_instance *h, cudaStream_t st, int8_t *best_grid, int *best_s
 {
     Session &se = h->session;
     if (!se.active) return fail(h, PLSE_EINVAL, "plse_run_result: no run in progress");
+    int rc = run_drain(h);
+    if (rc) return rc;
     const int nv = h->nv, n = h->n;
     int fstar = nv, gens_done = 0;
     std::vector<uint8_t> Sstar_h((size_t)nv, 0);
@@ -485,6 +570,27 @@ int plse_run_step(plse_handle h, int generations, void *stream, int *done)
 {
     if (!h) return PLSE_EINVAL;
     return run_step(h, generations, (cudaStream_t)stream, done);
+}
+
+int plse_run_issue(plse_handle h, void *stream, int *issued)
+{
+    if (!h) return PLSE_EINVAL;
+    if (h->session.active && (cudaStream_t)stream != h->session.stream)
+        return fail(h, PLSE_EINVAL, "plse_run_issue: not the stream of plse_run_begin");
+    return run_issue(h, issued);
+}
+
+int plse_run_query(plse_handle h, int *done, int *generations, int *in_flight)
+{
+    if (!h) return PLSE_EINVAL;
+    Session &se = h->session;
+    if (!se.active) return fail(h, PLSE_EINVAL, "plse_run_query: no run in progress");
+    const int rc = run_poll(h, false);
+    if (rc) return rc;
+    if (done) *done = se.finished && se.polled == se.issued;
+    if (generations) *generations = se.gen;
+    if (in_flight) *in_flight = se.issued - se.polled;
+    return PLSE_OK;
 }
 
 int plse_run_result(plse_handle h, void *stream, int8_t *best_grid, int *best_score, plse_solve_stats *stats,

@@ -103,3 +103,26 @@ def batch_mix(count: int = 64, seed0: int = 4000):
         else:
             out.append(random_insertion(n, r, seed0 + k))
     return out
+
+
+def serve_mix(count: int = 200, seed0: int = 5000):
+    """Request mix of the serving workload: about a quarter LSC-style requests
+    (cyclic-delete, n in [60, 100]), the rest random insertion with n uniform
+    over {10..100}; r ~ U[0.3, 0.8]; request k uses seed seed0 + k."""
+    out = []
+    for k in range(count):
+        rng = np.random.default_rng(seed0 + k)
+        r = float(rng.uniform(0.3, 0.8))
+        if rng.random() < 0.25:
+            n = int(rng.integers(60, 101))
+            out.append(cyclic_delete(n, r, seed0 + k)[0])
+        else:
+            n = int(rng.integers(10, 101))
+            out.append(random_insertion(n, r, seed0 + k))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 5000):
+    """Arrival times (seconds from 0) of a Poisson process with `rate` per second."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libplse.so")
 
 PLSE_OK, PLSE_EINVAL, PLSE_ENOMEM, PLSE_ECUDA = 0, -1, -2, -3
 PLSE_EBUSY, PLSE_ECANCELLED, PLSE_ENOTSUP, PLSE_ECHECK = -4, -5, -6, -7
+PLSE_PENDING = 1
 LS_PHASE1, LS_PHASE2, LS_REPAIR, LS_PARTIALCOL = 1, 2, 4, 8
 MODE_PLITS, MODE_PARTIALCOL = 0, 1
 MATCH_NEAREST, MATCH_RANDOM = 0, 1
@@ -53,6 +54,23 @@ class SolveStats(C.Structure):
                 ("ms_total", C.c_double), ("ms_local_search", C.c_double), ("launches", C.c_int64)]
 
 
+class Job(C.Structure):
+    _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("iters", C.c_int64), ("seed", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("best_score", C.c_int32), ("stats", SolveStats),
+                ("ms_queue", C.c_double), ("ms_wall", C.c_double)]
+
+    def as_dict(self):
+        st = self.stats
+        return {"status": int(self.status), "score": int(self.best_score),
+                "generations": int(st.generations), "best_f": int(st.best_f),
+                "walks": st.walks.as_dict(), "ms_total": float(st.ms_total),
+                "ms_local_search": float(st.ms_local_search), "launches": int(st.launches),
+                "ms_queue": float(self.ms_queue), "ms_wall": float(self.ms_wall)}
+
+
 _lib = None
 
 # exported C symbols and their (restype, argtypes)
@@ -74,6 +92,17 @@ SIGNATURES = {
     "plse_run_begin": (C.c_int, [_vp, C.c_int, C.c_int, _i64, _u64, _vp]),
     "plse_run_step": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
     "plse_run_result": (C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int), C.POINTER(SolveStats), _vp]),
+    "plse_run_issue": (C.c_int, [_vp, _vp, C.POINTER(C.c_int)]),
+    "plse_run_query": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "plse_solve_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(Job), C.c_int, C.c_int, C.POINTER(_vp),
+                                   C.POINTER(Result)]),
+    "plse_server_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_vp)]),
+    "plse_server_submit": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(Job), C.POINTER(Params),
+                                     C.POINTER(C.c_int64)]),
+    "plse_server_poll": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, C.POINTER(Result)]),
+    "plse_server_cancel": (C.c_int, [_vp, C.c_int64]),
+    "plse_server_pending": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "plse_server_destroy": (None, [_vp]),
     "plse_init_population": (C.c_int, [_vp, C.c_int, _u64, _vp, _vp]),
     "plse_local_search": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _i64, _u64, C.c_int,
                                     _vp, _vp, _vp, _vp]),
@@ -210,6 +239,18 @@ class Instance:
         self._check(self.lib.plse_run_step(self.h, generations, _stream(stream), C.byref(done)))
         return bool(done.value)
 
+    def run_issue(self, stream=None) -> bool:
+        """Enqueues the run's next generation without waiting (plse_run_issue)."""
+        issued = C.c_int()
+        self._check(self.lib.plse_run_issue(self.h, _stream(stream), C.byref(issued)))
+        return bool(issued.value)
+
+    def run_query(self):
+        """(done, completed generations, generations in flight), never waits."""
+        done, gens, inflight = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.plse_run_query(self.h, C.byref(done), C.byref(gens), C.byref(inflight)))
+        return bool(done.value), int(gens.value), int(inflight.value)
+
     def run_result(self, stream=None, trace=False):
         grid = np.zeros((self.n, self.n), dtype=np.int8)
         score = C.c_int()
@@ -259,3 +300,88 @@ class Instance:
     def crossover(self, p, P, partner, dist, gen, seed, O, stream=None):
         self._check(self.lib.plse_crossover(self.h, p, _dptr(P), _dptr(partner), _dptr(dist),
                                             gen, seed, _dptr(O), _stream(stream)))
+
+
+def _job(pop, generations, iters, seed):
+    return Job(int(pop), int(generations), int(iters), int(seed))
+
+
+def solve_batch(instances, jobs, max_inflight=0):
+    """plse_solve_batch: job i = (pop, generations, iters, seed) on instances[i].
+    Returns (list of result dicts with 'best_grid', first error code)."""
+    count = len(instances)
+    lib = load()
+    hs = (_vp * count)(*[inst.h for inst in instances])
+    js = (Job * count)(*[_job(*j) for j in jobs])
+    grids = [np.zeros((inst.n, inst.n), dtype=np.int8) for inst in instances]
+    gp = (_vp * count)(*[g.ctypes.data for g in grids])
+    res = (Result * count)()
+    rc = lib.plse_solve_batch(hs, js, count, max_inflight, gp, res)
+    out = []
+    for i in range(count):
+        d = res[i].as_dict()
+        d["best_grid"] = grids[i]
+        out.append(d)
+    return out, rc
+
+
+class Server:
+    """plse_server_*: requests admitted into `max_inflight` concurrent runs on
+    the current device, served by the library's own host thread."""
+
+    def __init__(self, max_inflight=8, max_queue=1024):
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.plse_server_create(max_inflight, max_queue, C.byref(h))
+        if rc != PLSE_OK:
+            raise PlseError(rc, "plse_server_create")
+        self.h = h
+        self.sizes = {}
+
+    def submit(self, grid, pop, generations, iters, seed, params=None):
+        """Returns a ticket, or raises PlseError(PLSE_EBUSY) when the queue is full."""
+        grid = np.ascontiguousarray(grid, dtype=np.int8)
+        t = C.c_int64()
+        job = _job(pop, generations, iters, seed)
+        rc = self.lib.plse_server_submit(self.h, grid.shape[0], grid.ctypes.data, C.byref(job),
+                                         C.byref(params) if params is not None else None, C.byref(t))
+        if rc != PLSE_OK:
+            raise PlseError(rc, "plse_server_submit")
+        self.sizes[t.value] = grid.shape[0]
+        return t.value
+
+    def poll(self, ticket, wait_ms=0):
+        """None while pending, else the result dict (with 'best_grid')."""
+        n = self.sizes.get(ticket, 1)
+        grid = np.zeros((n, n), dtype=np.int8)
+        res = Result()
+        rc = self.lib.plse_server_poll(self.h, ticket, int(wait_ms), grid.ctypes.data, C.byref(res))
+        if rc == PLSE_PENDING:
+            return None
+        if rc != PLSE_OK:
+            raise PlseError(rc, "plse_server_poll")
+        self.sizes.pop(ticket, None)
+        d = res.as_dict()
+        d["best_grid"] = grid
+        return d
+
+    def cancel(self, ticket):
+        rc = self.lib.plse_server_cancel(self.h, ticket)
+        if rc != PLSE_OK:
+            raise PlseError(rc, "plse_server_cancel")
+
+    def pending(self):
+        q, c = C.c_int(), C.c_int()
+        self.lib.plse_server_pending(self.h, C.byref(q), C.byref(c))
+        return int(q.value), int(c.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.plse_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -47,3 +47,31 @@ def test_strerror_and_invalid_arguments_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.plse_create(0, None, ctypes.byref(h)) == -1          # rejected before any CUDA call
     assert lib.plse_create(200, None, ctypes.byref(h)) == -1
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """sizeof / offsetof of every struct in include/plse.h, as gcc lays it out,
+    equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2103_10453_gb300 import plse
+    structs = {"plse_params": plse.Params, "plse_walk_stats": plse.WalkStats,
+               "plse_solve_stats": plse.SolveStats, "plse_job": plse.Job, "plse_result": plse.Result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "plse.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(cls, f).offset, (cname, f)
