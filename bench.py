@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--batch-pop", type=int, default=1024)
     ap.add_argument("--generations", type=int, default=10,
                     help="generations per job of --batch and --serve")
-    ap.add_argument("--inflight", type=int, default=16)
+    ap.add_argument("--inflight", type=int, default=None,
+                    help="concurrent runs of --batch (default 16) and --serve (default 64)")
     ap.add_argument("--serve", action="store_true",
                     help="serving case instead of the benchmark: Poisson arrivals into the "
                          "library's request server, latency percentiles")
@@ -143,6 +144,14 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
+# DRAM bytes per tabu move of local_search_kernel, from one ncu capture of the
+# small steady case (bench.py --ls-case 0.3 --pop 1216 --ls-iters 3000):
+# dram__bytes_read.sum + dram__bytes_write.sum = 17.75 MB for 1.8116e6 moves.
+# Scaled to a benchmark launch by its moves; the counters belong to the kernel
+# as captured, so this is None whenever the kernel has changed since.
+LS_DRAM_BYTES_PER_MOVE = 17.75e6 / 1.8116e6
+
+
 def walk_bytes(w):
     """Algorithmic bytes of tabu moves (explicit-gamma accounting): per scanned
     candidate 1 B colour, per scanned (v, j) pair 1 B gamma + 2 B tabu expiry,
@@ -234,7 +243,10 @@ def run_gpu(args):
     roofline = {"bound": "smem", "achieved": round(achieved, 1) if achieved else None,
                 "peak": round(smem_peak, 1), "unit": "GB/s",
                 "frac": round(achieved / smem_peak, 4) if achieved else None,
-                "traffic": None,
+                "traffic": (round(LS_DRAM_BYTES_PER_MOVE * wdelta["moves"] / launches_ls)
+                            if LS_DRAM_BYTES_PER_MOVE else None),
+                "traffic_note": "DRAM bytes per launch scaled by moves from the ncu capture of the "
+                                "small steady case (profiles/)",
                 "kernel": "local_search_kernel",
                 "peak_source": "derived: %d SMs x 128 B/clk x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
                                % (sm_count, sm_max),
@@ -426,13 +438,14 @@ def run_batch_case(args):
     seq = [G.solve(*j, with_stats=True) for G, j in zip(insts, jobs)]
     t_seq = time.perf_counter() - t0
     t0 = time.perf_counter()
-    bat, rc = plse.solve_batch(insts, jobs, max_inflight=args.inflight)
+    inflight = args.inflight or 16
+    bat, rc = plse.solve_batch(insts, jobs, max_inflight=inflight)
     t_bat = time.perf_counter() - t0
     same = rc == 0 and all(a["score"] == b["score"] and np.array_equal(a["best_grid"], b["best_grid"])
                            and a["walks"] == b["walks"] for a, b in zip(seq, bat))
     moves = sum(r["walks"]["moves"] for r in bat)
     print(json.dumps({"case": "batch", "jobs": len(jobs), "population": args.batch_pop,
-                      "generations": args.generations, "max_inflight": args.inflight,
+                      "generations": args.generations, "max_inflight": inflight,
                       "sequential_s": round(t_seq, 3), "batched_s": round(t_bat, 3),
                       "speedup": round(t_seq / t_bat, 3), "identical": bool(same),
                       "moves": moves, "batched_moves_per_s": round(moves / t_bat, 1),
@@ -441,16 +454,6 @@ def run_batch_case(args):
           flush=True)
     for G in insts:
         G.close()
-
-
-def serve_pop(grid):
-    """Population of a serving request, fixed by its size alone: 2^16 / (empty
-    cells), rounded down to a power of two, within [32, 512]."""
-    empty = max(int((grid == 0).sum()), 1)
-    p = 32
-    while p * 2 <= 512 and p * 2 * empty <= (1 << 16):
-        p *= 2
-    return p
 
 
 def run_serve_case(args):
@@ -464,7 +467,8 @@ def run_serve_case(args):
     from paper_2103_10453_gb300 import inputs, plse
     grids = inputs.serve_mix(args.requests)
     arrivals = inputs.poisson_arrivals(args.requests, args.rate)
-    srv = plse.Server(max_inflight=args.inflight, max_queue=args.requests)
+    inflight = args.inflight or 64
+    srv = plse.Server(max_inflight=inflight, max_queue=args.requests)
     # warm-up request (module load, first allocations), not counted
     w = srv.submit(inputs.tiny_n10(), 32, 2, 100, 1)
     srv.poll(w, wait_ms=-1)
@@ -475,21 +479,28 @@ def run_serve_case(args):
         if ta > now:
             time.sleep(ta - now)
         empty = int((g == 0).sum())
-        tickets.append(srv.submit(g, serve_pop(g), args.generations, 10 * empty, 1))
+        tickets.append(srv.submit(g, inputs.serve_pop(g), args.generations, 10 * empty, 1))
     res = [srv.poll(t, wait_ms=-1) for t in tickets]
     t_all = time.perf_counter() - t0
     srv.close()
     lat = np.array([r["ms_wall"] for r in res])
     ok = sum(1 for r in res if r["status"] == 0)
+    errors = {}
+    for g, r in zip(grids, res):
+        if r["status"] != 0:
+            key = "%d: %s" % (r["status"], r["detail"][:80])
+            errors.setdefault(key, []).append(int(g.shape[0]))
     print(json.dumps({"case": "serve", "requests": args.requests, "rate_per_s": args.rate,
-                      "max_inflight": args.inflight, "generations": args.generations,
+                      "max_inflight": inflight, "generations": args.generations,
                       "ok": ok, "wall_s": round(t_all, 3), "solves_per_s": round(ok / t_all, 3),
                       "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
                                      "p90": round(float(np.percentile(lat, 90)), 1),
                                      "p99": round(float(np.percentile(lat, 99)), 1),
                                      "max": round(float(lat.max()), 1)},
                       "queue_ms_p50": round(float(np.percentile([r["ms_queue"] for r in res], 50)), 1),
-                      "moves": sum(r["walks"]["moves"] for r in res)}), flush=True)
+                      "moves": sum(r["walks"]["moves"] for r in res),
+                      "errors": {k: {"count": len(v), "n": sorted(set(v))[:10]} for k, v in errors.items()}}),
+          flush=True)
 
 
 def main():

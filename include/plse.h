@@ -184,6 +184,7 @@ typedef struct {
     plse_solve_stats stats;   /* as plse_solve_ex                               */
     double  ms_queue;         /* host wall time from submission to the start    */
     double  ms_wall;          /* host wall time from submission to completion   */
+    char    detail[128];      /* message of the job's error ("" on success)     */
 } plse_result;
 
 /* plse_solve_batch -- runs job i on handle hs[i] (with that handle's

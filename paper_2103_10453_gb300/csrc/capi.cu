@@ -137,7 +137,11 @@ int upload_instance(plse_instance *h)
     memcpy(img.data() + o_ac, h->allow_col.data(), 16 * (size_t)n);
     memcpy(img.data() + o_rp, h->row_ptr.data(), 4 * (size_t)(n + 1));
     memcpy(img.data() + o_cp, h->col_ptr.data(), 4 * (size_t)(n + 1));
-    e = cudaMemcpy(h->inst_mem, img.data(), off, cudaMemcpyHostToDevice);
+    // A pageable host-to-device cudaMemcpy may return before its DMA has landed,
+    // and it is ordered only on the legacy default stream: wait for it, so that
+    // kernels on any stream (non-blocking ones included) see the whole image.
+    e = cudaMemcpyAsync(h->inst_mem, img.data(), off, cudaMemcpyHostToDevice, cudaStreamLegacy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) return cuda_fail(h, e, "instance upload");
     uint8_t *b = static_cast<uint8_t *>(h->inst_mem);
     DevInst &I = h->di;
@@ -231,6 +235,8 @@ int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
     }
     rc = grow(h, ws.TC, ws.TC_cap, (size_t)slots * h->di.nv, false, st);   // reset by every phase
     if (rc) return rc;
+    rc = grow(h, ws.LIST, ws.LIST_cap, (size_t)slots * h->di.nv, false, st); // rebuilt by every phase
+    if (rc) return rc;
     rc = grow(h, ws.slot_clock, ws.clock_cap, (size_t)slots, true, st);
     if (rc) return rc;
     return grow(h, ws.counters, ws.counters_cap, 8, true, st);
@@ -271,6 +277,7 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     if (rc) return rc;
     a.G = h->ws.G;
     a.TC = h->ws.TC;
+    a.LIST = h->ws.LIST;
     a.slot_clock = h->ws.slot_clock;
     a.work_counter = h->ws.counters;
     a.error_flag = h->ws.counters + 1;
@@ -349,6 +356,7 @@ void plse_destroy(plse_handle h)
     Workspace &ws = h->ws;
     if (ws.G) cudaFree(ws.G);
     if (ws.TC) cudaFree(ws.TC);
+    if (ws.LIST) cudaFree(ws.LIST);
     if (ws.slot_clock) cudaFree(ws.slot_clock);
     if (ws.counters) cudaFree(ws.counters);
     delete h;
@@ -409,7 +417,8 @@ int plse_sync(plse_handle h, void *stream)
     e = cudaMemcpy(&flag, h->ws.counters + 1, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "plse_sync");
     if (flag) {
-        cudaMemset(h->ws.counters + 1, 0, sizeof(int));
+        cudaMemsetAsync(h->ws.counters + 1, 0, sizeof(int), (cudaStream_t)stream);
+        cudaStreamSynchronize((cudaStream_t)stream);
         return fail(h, PLSE_ECHECK, "a device-side consistency check failed (flag %d)", flag);
     }
     return PLSE_OK;

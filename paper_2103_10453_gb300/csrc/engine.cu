@@ -12,6 +12,7 @@
 // instance, parameters, pop, generations, iters and seed), never of the mix,
 // because no device state is shared between handles.
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -37,6 +38,13 @@ bool job_valid(const plse_job &j)
 {
     return j.pop >= 2 && j.pop <= 65535 && j.generations >= 0 && j.generations <= 65534 && j.iters >= 0 &&
            j.iters <= (1ll << 30);
+}
+
+void note_detail(plse_result &r, const plse_instance *h)
+{
+    const char *msg = h ? h->err.c_str() : "";
+    if (!*msg) msg = plse_strerror(r.status);
+    snprintf(r.detail, sizeof(r.detail), "%s", msg);
 }
 
 // One job occupying a stream slot.
@@ -69,9 +77,10 @@ bool advance(Active &a, bool &progressed)
     if (rc == PLSE_OK) {
         rc = run_result(h, a.st, a.grid_out, &r.best_score, &r.stats, nullptr);
         r.status = rc ? rc : (a.cancel && !se.finished ? PLSE_ECANCELLED : PLSE_OK);
-    } else {
-        run_drain(h);
     }
+    if (r.status != PLSE_OK) note_detail(r, h);
+    // nothing of the job may still run when its handle is released or reused
+    cudaStreamSynchronize(a.st);
     se.active = 0;
     return true;
 }
@@ -126,6 +135,7 @@ extern "C" int plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count
                 r.ms_queue = t_start[i];
                 if (!job_valid(jobs[i])) {
                     r.status = fail(hs[i], PLSE_EINVAL, "plse_solve_batch: invalid job %d", i);
+                    note_detail(r, hs[i]);
                     r.ms_wall = ms_between(t0, Clock::now());
                     --remaining;
                     continue;
@@ -134,6 +144,8 @@ extern "C" int plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count
                                          streams[s]);
                 if (rc) {
                     r.status = rc;
+                    note_detail(r, hs[i]);
+                    cudaStreamSynchronize(streams[s]);
                     hs[i]->session.active = 0;
                     r.ms_wall = ms_between(t0, Clock::now());
                     --remaining;
@@ -271,6 +283,7 @@ struct plse_server_s {
                 r.res.ms_queue = ms_between(r.req.arrival, Clock::now());
                 if (r.req.cancel) {
                     r.res.status = PLSE_ECANCELLED;
+                    note_detail(r.res, nullptr);
                     finish(r);
                     continue;
                 }
@@ -283,6 +296,8 @@ struct plse_server_s {
                 r.a = Active{h, streams[s], r.grid.data(), &r.res, false};
                 if (rc) {
                     r.res.status = rc;
+                    note_detail(r.res, h);
+                    cudaStreamSynchronize(streams[s]);
                     if (h) h->session.active = 0;
                     finish(r);
                     continue;

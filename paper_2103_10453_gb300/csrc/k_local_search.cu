@@ -68,6 +68,11 @@ __device__ __forceinline__ int tenure_div(const LSArgs &a, int x)
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ inline int colour_words(int n) { return n < 32 ? 1 : n < 64 ? 2 : n < 96 ? 3 : 4; }
 
+// threads per block of the local search: 12 one-warp walks when one block is
+// resident per SM (n >= 64, register-limited at 168), 8 when two are (n < 64)
+template <int NWC>
+constexpr int kMaxThreads = NWC >= 3 ? 384 : 256;
+
 __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
 {
     const int cw = colour_words(I.n);
@@ -79,9 +84,8 @@ __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
     p.off_KP = o;     o += 32 * (size_t)I.n * cw;
     p.off_cmask = o;  o += 4 * (size_t)I.nw;
     p.off_lmask = o;  o += 4 * (size_t)I.nw;
-    p.off_list = align16(o);
-    o = align16(p.off_list + 2 * (size_t)I.nv);
-    p.off_red = o;
+    p.off_red = align16(o);
+    o = p.off_red;
     o = p.off_red + 8 * 2 * (size_t)warps + 4 * 2 * (size_t)warps + 4 * 16;
     p.slot = align16(o);
     return p;
@@ -93,7 +97,7 @@ struct Slot {
     uint32_t *RP, *KP;          // colour-count bit planes [n][cw][8] per row / per column
     uint32_t *cmask;            // candidate bitmask [nw]
     uint32_t *lmask;            // vertices present in the candidate list [nw]
-    uint16_t *list;             // candidate list (may hold stale entries) [nv]
+    uint16_t *list;             // candidate list (may hold stale entries) [nv], global memory
     uint2 *tc;                  // tabu cache [nv] in global memory (L1-resident for the candidates):
                                 // x = e0 | e1 << 16, y = c0 | c1 << 8 | emax << 16
     unsigned long long *red;    // [2][NW] best key per warp (double-buffered)
@@ -136,7 +140,7 @@ __device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I)
     c.s.KP = reinterpret_cast<uint32_t *>(sb + p.off_KP);
     c.s.cmask = reinterpret_cast<uint32_t *>(sb + p.off_cmask);
     c.s.lmask = reinterpret_cast<uint32_t *>(sb + p.off_lmask);
-    c.s.list = reinterpret_cast<uint16_t *>(sb + p.off_list);
+    c.s.list = nullptr;         // set once the walk slot is known
     c.s.tc = nullptr;           // set once the walk slot is known
     c.s.red = reinterpret_cast<unsigned long long *>(sb + p.off_red);
     c.s.red_cnt = reinterpret_cast<int *>(sb + p.off_red + 16 * NW);
@@ -1162,7 +1166,7 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
 }
 
 template <int NWC, int NW>
-__global__ void __launch_bounds__(256, NWC >= 3 ? 1 : 2) local_search_kernel(const DevInst I, const LSArgs a, int walks)
+__global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_search_kernel(const DevInst I, const LSArgs a, int walks)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     if (a.skip && *a.skip) return;
@@ -1178,6 +1182,7 @@ __global__ void __launch_bounds__(256, NWC >= 3 ? 1 : 2) local_search_kernel(con
     const int slot = blockIdx.x * walks + c.g;
     uint32_t *G = a.G + (size_t)slot * I.nv * I.n1p;
     c.s.tc = a.TC + (size_t)slot * I.nv;
+    c.s.list = a.LIST + (size_t)slot * I.nv;
 
     for (;;) {
         if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);
@@ -1316,9 +1321,11 @@ LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps, i
     int max_smem = 0, sms = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    // one block per SM holding as many walk slots as fit (at most 256 threads)
+    // one block per SM holding as many walk slots as fit (at most 384 threads at
+    // n >= 64, where one block is resident per SM; 256 below, with two blocks)
     long long walks = ((long long)max_smem - (long long)p.inst) / (long long)p.slot;
-    walks = std::min<long long>(walks, 256 / (32 * L.warps));
+    const int max_threads = L.colour_words >= 3 ? kMaxThreads<3> : kMaxThreads<1>;
+    walks = std::min<long long>(walks, std::max(1, max_threads / (32 * L.warps)));
     if (max_walks > 0) walks = std::min<long long>(walks, max_walks);
     if (walks < 1) {
         L.blocks = 0;

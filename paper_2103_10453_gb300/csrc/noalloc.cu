@@ -8,8 +8,8 @@
 // loop that must not hit the implicit device-wide synchronisation of
 // cudaMalloc / cudaFree.  This entry point serves them: it calls no cudaMalloc,
 // cudaFree or allocating library routine.  Its scratch (the evicted-tabu
-// tables, the tabu caches, the per-slot clocks, the walk counter and the check
-// flag) lives in
+// tables, the tabu caches, the candidate lists, the per-slot clocks, the walk
+// counter and the check flag) lives in
 // the file-scope array below, kNoAllocScratchBytes bytes on every GPU that loads
 // the library, held until the process exits.
 //
@@ -81,9 +81,9 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     if (rc) return rc;
 
     // walk slots that fit: each needs an evicted-tabu table (4 * |V| * n1p bytes),
-    // a tabu cache (8 * |V| bytes) and a clock word
-    const size_t table_bytes = 4 * (size_t)h->di.nv * h->di.n1p + 8 * (size_t)h->di.nv;
-    const size_t max_slots = (kNoAllocScratchBytes - kCounterBytes - 512) / (table_bytes + 4);   // 512: alignment
+    // a tabu cache (8 * |V| bytes), a candidate list (2 * |V| bytes) and a clock word
+    const size_t table_bytes = 4 * (size_t)h->di.nv * h->di.n1p + 10 * (size_t)h->di.nv;
+    const size_t max_slots = (kNoAllocScratchBytes - kCounterBytes - 1024) / (table_bytes + 4);   // 1024: alignment
     if (max_slots < 1)
         return fail(h, PLSE_ENOTSUP,
                     "plse_local_search_noalloc: one walk slot needs %zu bytes of scratch, more than the %zu "
@@ -99,15 +99,17 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
         if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: no walk slot fits");
     }
     const size_t slots = (size_t)L.slots();
-    // layout: [counters][slot clocks][evicted-tabu tables][tabu caches]; the
-    // first three must start at zero, the caches are reset by every phase
+    // layout: [counters][slot clocks][evicted-tabu tables][tabu caches][lists];
+    // the first three must start at zero, caches and lists are reset by every phase
     int *counters = reinterpret_cast<int *>(scratch);
     uint32_t *clocks = reinterpret_cast<uint32_t *>(scratch + kCounterBytes);
     const size_t tables_off = (kCounterBytes + 4 * slots + 255) & ~size_t(255);
     uint32_t *tables = reinterpret_cast<uint32_t *>(scratch + tables_off);
     const size_t tc_off = (tables_off + slots * 4 * (size_t)h->di.nv * h->di.n1p + 255) & ~size_t(255);
     uint2 *tcache = reinterpret_cast<uint2 *>(scratch + tc_off);
-    const size_t used = tc_off + slots * 8 * (size_t)h->di.nv;
+    const size_t list_off = (tc_off + slots * 8 * (size_t)h->di.nv + 255) & ~size_t(255);
+    uint16_t *lists = reinterpret_cast<uint16_t *>(scratch + list_off);
+    const size_t used = list_off + slots * 2 * (size_t)h->di.nv;
     if (used > kNoAllocScratchBytes) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: scratch overflow");
     e = cudaMemsetAsync(scratch, 0, tc_off, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "plse_local_search_noalloc: clear scratch");
@@ -138,6 +140,7 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     a.stats = stats;
     a.G = tables;
     a.TC = tcache;
+    a.LIST = lists;
     a.slot_clock = clocks;
     a.work_counter = counters;
     a.error_flag = counters + 1;

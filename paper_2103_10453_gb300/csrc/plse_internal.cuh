@@ -56,6 +56,7 @@ struct LSArgs {
     // scratch (global memory owned by the handle's workspace)
     uint32_t *G;                  // [slots][nv * n1p] evicted tabu expiries (absolute clock)
     uint2 *TC;                    // [slots][nv] two-entry tabu caches (relative clock)
+    uint16_t *LIST;               // [slots][nv] candidate lists
     uint32_t *slot_clock;         // [slots] next free clock value of each slot
     int *work_counter;            // dynamic walk scheduler, zeroed before launch
     int *error_flag;              // nonzero after a failed device bound check
@@ -75,7 +76,7 @@ struct LSLaunch {
 struct SmemPlan {
     size_t inst;       // vertex coordinates and allowed-colour masks
     size_t slot;       // one walk: colouring, count planes, candidate set, tabu cache, scalars
-    size_t off_S, off_RP, off_KP, off_cmask, off_lmask, off_list, off_red;   // within a slot
+    size_t off_S, off_RP, off_KP, off_cmask, off_lmask, off_red;   // within a slot
     size_t total(int walks) const { return inst + slot * (size_t)walks; }
 };
 

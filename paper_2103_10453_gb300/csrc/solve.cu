@@ -498,7 +498,8 @@ int run_result(plse_instance *h, cudaStream_t st, int8_t *best_grid, int *best_s
         int flag = 0;
         CK(cudaMemcpy(&flag, h->ws.counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
         if (flag) {
-            cudaMemset(h->ws.counters + 1, 0, sizeof(int));
+            cudaMemsetAsync(h->ws.counters + 1, 0, sizeof(int), st);
+            cudaStreamSynchronize(st);
             return fail(h, PLSE_ECHECK, "a local-search consistency check failed");
         }
     }

@@ -126,3 +126,13 @@ def poisson_arrivals(count: int, rate: float, seed: int = 5000):
     """Arrival times (seconds from 0) of a Poisson process with `rate` per second."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
+def serve_pop(grid) -> int:
+    """Population of a serving request, fixed by its size alone (never by load):
+    2^16 / (empty cells), rounded down to a power of two, within [32, 512]."""
+    empty = max(int((np.asarray(grid) == 0).sum()), 1)
+    p = 32
+    while p * 2 <= 512 and p * 2 * empty <= (1 << 16):
+        p *= 2
+    return p

@@ -60,7 +60,7 @@ class Job(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("best_score", C.c_int32), ("stats", SolveStats),
-                ("ms_queue", C.c_double), ("ms_wall", C.c_double)]
+                ("ms_queue", C.c_double), ("ms_wall", C.c_double), ("detail", C.c_char * 128)]
 
     def as_dict(self):
         st = self.stats
@@ -68,7 +68,8 @@ class Result(C.Structure):
                 "generations": int(st.generations), "best_f": int(st.best_f),
                 "walks": st.walks.as_dict(), "ms_total": float(st.ms_total),
                 "ms_local_search": float(st.ms_local_search), "launches": int(st.launches),
-                "ms_queue": float(self.ms_queue), "ms_wall": float(self.ms_wall)}
+                "ms_queue": float(self.ms_queue), "ms_wall": float(self.ms_wall),
+                "detail": self.detail.decode(errors="replace")}
 
 
 _lib = None

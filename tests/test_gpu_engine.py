@@ -169,3 +169,18 @@ def test_server_admission_cancel_and_invalid_grid(plse):
     srv.submit(long_grid, 256, 3000, 4000, 2, params=no_stop)
     srv.submit(long_grid, 256, 3000, 4000, 3, params=no_stop)
     srv.close()
+
+
+def test_server_mixed_sizes_against_solve_alone(plse):
+    """Requests of the serving mix (n from 10 to 96, populations 32 to 512) admitted
+    while others run: each handle is created and launched on a non-blocking
+    stream at once, so the instance upload must be complete before its kernels."""
+    gs = inputs.serve_mix(24)
+    srv = plse.Server(max_inflight=16, max_queue=64)
+    jobs = [(inputs.serve_pop(g), 2, 2 * int((g == 0).sum()), 1) for g in gs]
+    tickets = [srv.submit(g, *job) for g, job in zip(gs, jobs)]
+    outs = [srv.poll(t, wait_ms=-1) for t in tickets]
+    srv.close()
+    for g, job, r in zip(gs, jobs, outs):
+        assert r["status"] == 0, r["detail"]
+        same(r, alone(plse, g, job))
