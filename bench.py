@@ -59,7 +59,15 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving case instead of the benchmark: Poisson arrivals into the "
                          "library's request server, latency percentiles")
+    ap.add_argument("--pop-sweep", action="store_true",
+                    help="population-size sweep on a synthetic (60, 0.7) instance: throughput "
+                         "and best score per population size")
+    ap.add_argument("--lsc", action="store_true",
+                    help="Latin square completion case: time to a complete square on "
+                         "cyclic-delete instances, n in {50, 60, 70}, r in {0.3..0.8}")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--serve-compare", action="store_true",
+                    help="with --serve: also run the same jobs at once through plse_solve_batch")
     ap.add_argument("--rate", type=float, default=20.0)
     return ap.parse_args()
 
@@ -484,7 +492,21 @@ def run_serve_case(args):
     t_all = time.perf_counter() - t0
     srv.close()
     lat = np.array([r["ms_wall"] for r in res])
+    run_ms = np.array([r["ms_wall"] - r["ms_queue"] for r in res])
+    dev_ms = np.array([r["ms_total"] for r in res])
     ok = sum(1 for r in res if r["status"] == 0)
+    compare = None
+    if args.serve_compare:
+        # the same jobs with every request present at once, through plse_solve_batch
+        insts = [plse.Instance(g) for g in grids]
+        jobs = [(inputs.serve_pop(g), args.generations, 10 * int((g == 0).sum()), 1) for g in grids]
+        t1 = time.perf_counter()
+        bat, rc = plse.solve_batch(insts, jobs, max_inflight=inflight)
+        compare = {"batch_wall_s": round(time.perf_counter() - t1, 3), "rc": rc,
+                   "identical": all(a["score"] == b["score"] and a["walks"] == b["walks"]
+                                    for a, b in zip(res, bat))}
+        for G in insts:
+            G.close()
     errors = {}
     for g, r in zip(grids, res):
         if r["status"] != 0:
@@ -498,9 +520,64 @@ def run_serve_case(args):
                                      "p99": round(float(np.percentile(lat, 99)), 1),
                                      "max": round(float(lat.max()), 1)},
                       "queue_ms_p50": round(float(np.percentile([r["ms_queue"] for r in res], 50)), 1),
+                      "run_ms": {"p50": round(float(np.percentile(run_ms, 50)), 1),
+                                 "p90": round(float(np.percentile(run_ms, 90)), 1)},
+                      "device_ms": {"p50": round(float(np.percentile(dev_ms, 50)), 1),
+                                    "p90": round(float(np.percentile(dev_ms, 90)), 1)},
+                      "generations_mean": round(float(np.mean([r["generations"] for r in res])), 2),
+                      "same_jobs_as_one_batch": compare,
                       "moves": sum(r["walks"]["moves"] for r in res),
                       "errors": {k: {"count": len(v), "n": sorted(set(v))[:10]} for k, v in errors.items()}}),
           flush=True)
+
+
+def run_pop_sweep(args):
+    """Population sizes 16 .. 16384 on one synthetic (n, r) = (60, 0.7) instance
+    (random insertion, seed 6000), --generations generations (default 10 here:
+    pass it), phase-1 iterations 10|V|, optimality stop off: tabu moves per
+    device second and the best score after the run, per population size."""
+    from paper_2103_10453_gb300 import inputs, plse
+    G = plse.Instance(inputs.random_insertion(60, 0.7, 6000))
+    G.set_params(plse.default_params(stop_at_bound=0))
+    rows = []
+    for pop in (16, 64, 256, 1024, 4096, 16384):
+        res = G.solve(pop, args.generations, 10 * G.nv, 1, with_stats=True)
+        rows.append({"pop": pop, "best_score": res["score"], "ms_total": round(res["ms_total"], 2),
+                     "ms_per_generation": round(res["ms_total"] / max(res["generations"], 1), 2),
+                     "moves_per_s": round(res["walks"]["moves"] / (res["ms_local_search"] / 1e3), 1)})
+    print(json.dumps({"case": "pop_sweep", "n": 60, "r": 0.7, "nv": G.nv, "ub": G.ub,
+                      "generations": args.generations, "rows": rows}), flush=True)
+    G.close()
+
+
+def run_lsc_case(args):
+    """Latin square completion (App. B): cyclic-delete instances, which have a
+    complete square as witness, two per (n, r) with n in {50, 60, 70} and
+    r in {0.3, ..., 0.8} (seeds 7000 + k); population --batch-pop, at most
+    --generations generations, phase-1 iterations 10|V|, optimality stop on.
+    Solved fraction, generations and device time to the complete square."""
+    import numpy as np
+    from paper_2103_10453_gb300 import inputs, plse
+    rows, k = [], 0
+    for n in (50, 60, 70):
+        for r in (0.3, 0.4, 0.5, 0.6, 0.7, 0.8):
+            for rep in range(2):
+                grid = inputs.cyclic_delete(n, r, 7000 + k)[0]
+                k += 1
+                G = plse.Instance(grid)
+                res = G.solve(args.batch_pop, args.generations, 10 * G.nv, 1, with_stats=True)
+                rows.append({"n": n, "r": r, "solved": res["score"] == n * n,
+                             "generations": res["generations"], "ms": round(res["ms_total"], 1)})
+                G.close()
+    solved = [x for x in rows if x["solved"]]
+    ms = np.array([x["ms"] for x in solved]) if solved else np.zeros(1)
+    print(json.dumps({"case": "lsc", "instances": len(rows), "solved": len(solved),
+                      "population": args.batch_pop, "max_generations": args.generations,
+                      "ms_to_solve": {"p50": round(float(np.percentile(ms, 50)), 1),
+                                      "p90": round(float(np.percentile(ms, 90)), 1),
+                                      "max": round(float(ms.max()), 1)},
+                      "generations_to_solve_max": max((x["generations"] for x in solved), default=0),
+                      "rows": rows}), flush=True)
 
 
 def main():
@@ -511,6 +588,10 @@ def main():
         run_batch_case(args)
     elif args.serve:
         run_serve_case(args)
+    elif args.pop_sweep:
+        run_pop_sweep(args)
+    elif args.lsc:
+        run_lsc_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

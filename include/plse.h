@@ -54,7 +54,7 @@ typedef struct {
     int32_t phase2_iter_per_v;     /* phase-2 iterations per |V| (2)             */
     int32_t spacing_gamma;         /* Alg. 4 spacing D > |V|/gamma (10)          */
     int32_t beta;                  /* AUX parameter beta (20)                    */
-    int32_t mode;                  /* PLSE_MODE_PLITS or PLSE_MODE_PARTIALCOL    */
+    int32_t mode;                  /* PLSE_MODE_PLITS, _PARTIALCOL or _AUTO      */
     int32_t matching;              /* PLSE_MATCH_NEAREST or PLSE_MATCH_RANDOM    */
     int32_t crossover;             /* PLSE_XOVER_AUX or PLSE_XOVER_UX            */
     int32_t tested_cap;            /* tested-partner list capacity, 1..256 (64)  */
@@ -64,6 +64,8 @@ typedef struct {
 
 #define PLSE_MODE_PLITS       0    /* two-phase tabu search, Sec. 3.3            */
 #define PLSE_MODE_PARTIALCOL  1    /* Partial-MPMA local search, Sec. 3.7        */
+#define PLSE_MODE_AUTO        2    /* Partial-MPMA when at least 80% of the cells
+                                      are prefilled (Sec. 3.7), else PLITS        */
 #define PLSE_MATCH_NEAREST    0    /* nearest untested partner, Sec. 3.5.1       */
 #define PLSE_MATCH_RANDOM     1    /* random partner (ablation of Sec. 5.3)      */
 #define PLSE_XOVER_AUX        0    /* asymmetric uniform crossover, Eq. 10       */

@@ -123,7 +123,7 @@ int upload_instance(plse_instance *h)
     const size_t o_cv = off; off = up256(off + 2 * (size_t)nv + 2);
     const size_t o_ar = off; off = up256(off + 16 * (size_t)n);
     const size_t o_ac = off; off = up256(off + 16 * (size_t)n);
-    cudaError_t e = cudaMalloc(&h->inst_mem, off);
+    cudaError_t e = dev_malloc(&h->inst_mem, off, cudaStreamLegacy);
     if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "instance upload: %s", cudaGetErrorString(e));
     std::vector<uint8_t> img(off, 0);
     if (nv) {
@@ -137,9 +137,9 @@ int upload_instance(plse_instance *h)
     memcpy(img.data() + o_ac, h->allow_col.data(), 16 * (size_t)n);
     memcpy(img.data() + o_rp, h->row_ptr.data(), 4 * (size_t)(n + 1));
     memcpy(img.data() + o_cp, h->col_ptr.data(), 4 * (size_t)(n + 1));
-    // A pageable host-to-device cudaMemcpy may return before its DMA has landed,
-    // and it is ordered only on the legacy default stream: wait for it, so that
-    // kernels on any stream (non-blocking ones included) see the whole image.
+    // A pageable host-to-device copy may return before its DMA has landed, and
+    // the legacy stream orders it (and the allocation) for blocking streams only:
+    // wait for both, so that kernels on any stream see the whole image.
     e = cudaMemcpyAsync(h->inst_mem, img.data(), off, cudaMemcpyHostToDevice, cudaStreamLegacy);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) return cuda_fail(h, e, "instance upload");
@@ -168,7 +168,7 @@ int check_params(plse_instance *h, const plse_params &p)
 {
     if (p.alpha_num < 0 || p.alpha_den < 1 || p.tenure_rand < 1 || p.phase1_phi2 < 1 ||
         p.phase2_phi2_per_v < 1 || p.phase2_iter_per_v < 0 || p.spacing_gamma < 1 || p.beta < 1 ||
-        (p.mode != PLSE_MODE_PLITS && p.mode != PLSE_MODE_PARTIALCOL) ||
+        (p.mode != PLSE_MODE_PLITS && p.mode != PLSE_MODE_PARTIALCOL && p.mode != PLSE_MODE_AUTO) ||
         (p.matching != PLSE_MATCH_NEAREST && p.matching != PLSE_MATCH_RANDOM) ||
         (p.crossover != PLSE_XOVER_AUX && p.crossover != PLSE_XOVER_UX) ||
         p.tested_cap < 1 || p.tested_cap > 256 || (p.stop_at_bound != 0 && p.stop_at_bound != 1))
@@ -212,9 +212,11 @@ template <typename T>
 static int grow(plse_instance *h, T *&ptr, size_t &cap, size_t need, bool zero, cudaStream_t st)
 {
     if (need <= cap) return PLSE_OK;
-    if (ptr) { cudaFree(ptr); ptr = nullptr; cap = 0; }
-    cudaError_t e = cudaMalloc(&ptr, need * sizeof(T));
-    if (e != cudaSuccess) { ptr = nullptr; return fail(h, PLSE_ENOMEM, "workspace: %s", cudaGetErrorString(e)); }
+    if (ptr) { dev_free(ptr, st); ptr = nullptr; cap = 0; }
+    void *q = nullptr;
+    cudaError_t e = dev_malloc(&q, need * sizeof(T), st);
+    if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "workspace: %s", cudaGetErrorString(e));
+    ptr = static_cast<T *>(q);
     if (zero) {
         e = cudaMemsetAsync(ptr, 0, need * sizeof(T), st);   // in order with the launch that needs it
         if (e != cudaSuccess) return cuda_fail(h, e, "workspace clear");
@@ -335,6 +337,7 @@ int plse_create(int n, const int8_t *grid, plse_handle *out)
     int rc = build_instance(h, n, grid);
     if (rc == PLSE_OK) {
         cudaError_t e = cudaGetDevice(&h->device);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done_ev, cudaEventDisableTiming);
         rc = (e != cudaSuccess) ? cuda_fail(h, e, "cudaGetDevice") : upload_instance(h);
     }
     if (rc == PLSE_OK) rc = check_exactness(h, h->params);
@@ -350,15 +353,19 @@ int plse_create(int n, const int8_t *grid, plse_handle *out)
 void plse_destroy(plse_handle h)
 {
     if (!h) return;
-    run_drain(h);            // nothing of the handle may still run on the device
-    release_solver(h);
-    if (h->inst_mem) cudaFree(h->inst_mem);
+    run_drain(h);
+    // free in stream order after the handle's last work, without waiting for it
+    const cudaStream_t st = cudaStreamLegacy;
+    if (h->done_recorded) cudaStreamWaitEvent(st, h->done_ev, 0);
+    release_solver(h, st);
+    dev_free(h->inst_mem, st);
     Workspace &ws = h->ws;
-    if (ws.G) cudaFree(ws.G);
-    if (ws.TC) cudaFree(ws.TC);
-    if (ws.LIST) cudaFree(ws.LIST);
-    if (ws.slot_clock) cudaFree(ws.slot_clock);
-    if (ws.counters) cudaFree(ws.counters);
+    dev_free(ws.G, st);
+    dev_free(ws.TC, st);
+    dev_free(ws.LIST, st);
+    dev_free(ws.slot_clock, st);
+    dev_free(ws.counters, st);
+    if (h->done_ev) cudaEventDestroy(h->done_ev);
     delete h;
 }
 
@@ -427,6 +434,7 @@ int plse_sync(plse_handle h, void *stream)
 int plse_init_population(plse_handle h, int pop, uint64_t seed, uint8_t *P, void *stream)
 {
     if (!h || pop < 0 || (pop > 0 && h->nv > 0 && !P)) return PLSE_EINVAL;
+    StreamScope scope(h, (cudaStream_t)stream);
     cudaError_t e = launch_init_population(h->di, pop, seed, P, (cudaStream_t)stream);
     return e == cudaSuccess ? PLSE_OK : cuda_fail(h, e, "init_population");
 }
@@ -441,6 +449,7 @@ int plse_local_search(plse_handle h, const uint8_t *S_in, uint8_t *S_out, int co
     if (count == 0) return PLSE_OK;
     if (!S_in || !S_out) return fail(h, PLSE_EINVAL, "plse_local_search: null buffer");
     cudaStream_t st = (cudaStream_t)stream;
+    StreamScope scope(h, st);
     if (h->nv == 0) {
         if (f_out) cudaMemsetAsync(f_out, 0, sizeof(int32_t) * count, st);
         if (F_out) cudaMemsetAsync(F_out, 0, sizeof(int64_t) * count, st);

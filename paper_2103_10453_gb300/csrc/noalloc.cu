@@ -67,6 +67,7 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     if (count == 0) return PLSE_OK;
     if (!S_in || !S_out) return fail(h, PLSE_EINVAL, "plse_local_search_noalloc: null buffer");
     cudaStream_t st = (cudaStream_t)stream;
+    StreamScope scope(h, st);
     if (h->nv == 0) {
         if (f_out && cudaMemsetAsync(f_out, 0, sizeof(int32_t) * count, st) != cudaSuccess) return PLSE_ECUDA;
         if (F_out && cudaMemsetAsync(F_out, 0, sizeof(int64_t) * count, st) != cudaSuccess) return PLSE_ECUDA;

@@ -64,6 +64,8 @@ struct plse_instance {
     uint32_t *step_planes = nullptr;   // bit planes for the population step entry points
     size_t step_planes_cap = 0;
     plse::PopScratch step_ps;          // Alg. 4 scratch for plse_pop_update
+    cudaEvent_t done_ev = nullptr;     // recorded after the handle's latest enqueued work
+    bool done_recorded = false;
     std::string err;
 };
 
@@ -76,7 +78,24 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
                          int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
                          int64_t *F_out, plse_walk_stats *stats, cudaStream_t st,
                          const int *skip = nullptr);
-void release_solver(plse_instance *h);
+void release_solver(plse_instance *h, cudaStream_t st);
+
+// device memory of handles (stream-ordered pool) and pinned flag slots (devmem.cu)
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+int *pinned_slot_get();          // 16 bytes of pinned host memory, zeroed
+void pinned_slot_put(int *slot);
+
+// Orders work enqueued on st after the handle's earlier work (any stream) and
+// records the handle's event after it; one per call that enqueues work.
+struct StreamScope {
+    plse_instance *h;
+    cudaStream_t st;
+    StreamScope(plse_instance *h, cudaStream_t st);
+    ~StreamScope();
+    StreamScope(const StreamScope &) = delete;
+    StreamScope &operator=(const StreamScope &) = delete;
+};
 
 // resumable run of Alg. 2 (solve.cu).  run_issue enqueues one more generation
 // when fewer than two are in flight (never waits); run_poll consumes completed

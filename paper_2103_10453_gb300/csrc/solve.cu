@@ -190,82 +190,84 @@ __global__ void init_ctrl_kernel(Ctrl *ctrl, int nv, int ftarget)
 }
 
 template <typename T>
-int dalloc(plse_instance *h, T *&p, size_t n)
+int dalloc(plse_instance *h, T *&p, size_t n, cudaStream_t st)
 {
-    if (p) { cudaFree(p); p = nullptr; }
+    if (p) { dev_free(p, st); p = nullptr; }
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
-    if (e != cudaSuccess) { p = nullptr; return fail(h, PLSE_ENOMEM, "solver allocation: %s", cudaGetErrorString(e)); }
+    void *q = nullptr;
+    cudaError_t e = dev_malloc(&q, n * sizeof(T), st);
+    if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "solver allocation: %s", cudaGetErrorString(e));
+    p = static_cast<T *>(q);
     return PLSE_OK;
+}
+
+static_assert(2 * kGenDepth <= 4, "the host flag slot holds two generations");
+
+}  // namespace
+
+void free_pop_scratch(PopScratch &ps, cudaStream_t st);
+
+namespace {
+
+// device buffers, events and the pinned flag slot of a solver state
+void free_solver_state(SolverState *s, cudaStream_t st)
+{
+    for (int k = 0; k < 2; ++k) {
+        dev_free(s->Pall[k], st); dev_free(s->planes[k], st); dev_free(s->e[k], st);
+        dev_free(s->uid[k], st); dev_free(s->tested[k], st); dev_free(s->tcount[k], st);
+    }
+    dev_free(s->SO, st); dev_free(s->fprime, st); dev_free(s->sel, st); dev_free(s->partner, st);
+    dev_free(s->dist, st); dev_free(s->wstats, st); dev_free(s->ctrl, st); dev_free(s->Sstar, st);
+    dev_free(s->trace, st);
+    free_pop_scratch(s->ps, st);
+    for (auto &ev : s->ev) if (ev) cudaEventDestroy(ev);
+    for (auto &g : s->gev)
+        for (auto &ev : g) if (ev) cudaEventDestroy(ev);
+    pinned_slot_put(s->hflag);
+    delete s;
 }
 
 }  // namespace
 
-int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p)
+int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p, cudaStream_t st)
 {
     if (p <= ps.cap_p) return PLSE_OK;
     const int m = 2 * p, nchunks = (m + kChunk - 1) / kChunk;
     int rc;
-    if ((rc = dalloc(h, ps.order, m)) || (rc = dalloc(h, ps.mind, m)) || (rc = dalloc(h, ps.acc, p)) ||
-        (rc = dalloc(h, ps.rej, m)) || (rc = dalloc(h, ps.Dloc, (size_t)nchunks * kChunk * kChunk)) ||
-        (rc = dalloc(h, ps.sel_state, 1)))
+    if ((rc = dalloc(h, ps.order, m, st)) || (rc = dalloc(h, ps.mind, m, st)) || (rc = dalloc(h, ps.acc, p, st)) ||
+        (rc = dalloc(h, ps.rej, m, st)) || (rc = dalloc(h, ps.Dloc, (size_t)nchunks * kChunk * kChunk, st)) ||
+        (rc = dalloc(h, ps.sel_state, 1, st)))
         return rc;
     ps.cap_p = p;
     return PLSE_OK;
 }
 
-void free_pop_scratch(PopScratch &ps)
+void free_pop_scratch(PopScratch &ps, cudaStream_t st)
 {
-    cudaFree(ps.order); cudaFree(ps.mind); cudaFree(ps.acc); cudaFree(ps.rej);
-    cudaFree(ps.Dloc); cudaFree(ps.sel_state);
+    dev_free(ps.order, st); dev_free(ps.mind, st); dev_free(ps.acc, st); dev_free(ps.rej, st);
+    dev_free(ps.Dloc, st); dev_free(ps.sel_state, st);
     ps = PopScratch();
 }
 
-void release_solver(plse_instance *h)
+void release_solver(plse_instance *h, cudaStream_t st)
 {
-    SolverState *s = h->solver;
-    if (!s) return;
-    for (int k = 0; k < 2; ++k) {
-        cudaFree(s->Pall[k]); cudaFree(s->planes[k]); cudaFree(s->e[k]);
-        cudaFree(s->uid[k]); cudaFree(s->tested[k]); cudaFree(s->tcount[k]);
-    }
-    cudaFree(s->SO); cudaFree(s->fprime); cudaFree(s->sel); cudaFree(s->partner); cudaFree(s->dist);
-    cudaFree(s->wstats); cudaFree(s->ctrl); cudaFree(s->Sstar); cudaFree(s->trace);
-    free_pop_scratch(s->ps);
-    for (auto &ev : s->ev) if (ev) cudaEventDestroy(ev);
-    for (auto &g : s->gev)
-        for (auto &ev : g) if (ev) cudaEventDestroy(ev);
-    if (s->hflag) cudaFreeHost(s->hflag);
-    delete s;
+    if (h->solver) free_solver_state(h->solver, st);
     h->solver = nullptr;
     // step scratch
-    cudaFree(h->step_planes);
+    dev_free(h->step_planes, st);
     h->step_planes = nullptr;
     h->step_planes_cap = 0;
-    free_pop_scratch(h->step_ps);
+    free_pop_scratch(h->step_ps, st);
 }
 
-static int ensure_solver(plse_instance *h, int p, int gens)
+static int ensure_solver(plse_instance *h, int p, int gens, cudaStream_t st)
 {
     SolverState *s = h->solver;
     const int cap = h->params.tested_cap;
     if (s && s->cap_p >= p && s->cap_gens >= gens && s->tested_cap == cap) return PLSE_OK;
     if (s) {
         // keep the step scratch, rebuild the solver buffers
-        SolverState *old = s;
-        for (int k = 0; k < 2; ++k) {
-            cudaFree(old->Pall[k]); cudaFree(old->planes[k]); cudaFree(old->e[k]);
-            cudaFree(old->uid[k]); cudaFree(old->tested[k]); cudaFree(old->tcount[k]);
-        }
-        cudaFree(old->SO); cudaFree(old->fprime); cudaFree(old->sel); cudaFree(old->partner);
-        cudaFree(old->dist); cudaFree(old->wstats); cudaFree(old->ctrl); cudaFree(old->Sstar);
-        cudaFree(old->trace);
-        free_pop_scratch(old->ps);
-        for (auto &ev : old->ev) if (ev) cudaEventDestroy(ev);
-        for (auto &g : old->gev)
-            for (auto &ev : g) if (ev) cudaEventDestroy(ev);
-        if (old->hflag) cudaFreeHost(old->hflag);
-        delete old;
+        free_solver_state(s, st);
         h->solver = nullptr;
     }
     s = new SolverState();
@@ -274,27 +276,25 @@ static int ensure_solver(plse_instance *h, int p, int gens)
     const size_t PV = (size_t)p * I.nv, stride = (size_t)I.nw * I.nb;
     int rc;
     for (int k = 0; k < 2; ++k) {
-        if ((rc = dalloc(h, s->Pall[k], 2 * PV)) || (rc = dalloc(h, s->planes[k], 2 * (size_t)p * stride)) ||
-            (rc = dalloc(h, s->e[k], 2 * (size_t)p)) || (rc = dalloc(h, s->uid[k], (size_t)p)) ||
-            (rc = dalloc(h, s->tested[k], (size_t)p * cap)) || (rc = dalloc(h, s->tcount[k], (size_t)p)))
+        if ((rc = dalloc(h, s->Pall[k], 2 * PV, st)) || (rc = dalloc(h, s->planes[k], 2 * (size_t)p * stride, st)) ||
+            (rc = dalloc(h, s->e[k], 2 * (size_t)p, st)) || (rc = dalloc(h, s->uid[k], (size_t)p, st)) ||
+            (rc = dalloc(h, s->tested[k], (size_t)p * cap, st)) || (rc = dalloc(h, s->tcount[k], (size_t)p, st)))
             return rc;
     }
-    if ((rc = dalloc(h, s->SO, PV)) || (rc = dalloc(h, s->fprime, (size_t)p)) || (rc = dalloc(h, s->sel, (size_t)p)) ||
-        (rc = dalloc(h, s->partner, (size_t)p)) || (rc = dalloc(h, s->dist, (size_t)p)) ||
-        (rc = dalloc(h, s->wstats, (size_t)p)) || (rc = dalloc(h, s->ctrl, 1)) ||
-        (rc = dalloc(h, s->Sstar, (size_t)I.nv)) || (rc = dalloc(h, s->trace, (size_t)gens)))
+    if ((rc = dalloc(h, s->SO, PV, st)) || (rc = dalloc(h, s->fprime, (size_t)p, st)) ||
+        (rc = dalloc(h, s->sel, (size_t)p, st)) || (rc = dalloc(h, s->partner, (size_t)p, st)) ||
+        (rc = dalloc(h, s->dist, (size_t)p, st)) || (rc = dalloc(h, s->wstats, (size_t)p, st)) ||
+        (rc = dalloc(h, s->ctrl, 1, st)) || (rc = dalloc(h, s->Sstar, (size_t)I.nv, st)) ||
+        (rc = dalloc(h, s->trace, (size_t)gens, st)))
         return rc;
-    if ((rc = ensure_pop_scratch(h, s->ps, p))) return rc;
+    if ((rc = ensure_pop_scratch(h, s->ps, p, st))) return rc;
     for (auto &ev : s->ev)
         if (cudaEventCreate(&ev) != cudaSuccess) return fail(h, PLSE_ECUDA, "event create");
     for (auto &g : s->gev)
         for (auto &ev : g)
             if (cudaEventCreate(&ev) != cudaSuccess) return fail(h, PLSE_ECUDA, "event create");
-    if (cudaHostAlloc(reinterpret_cast<void **>(&s->hflag), sizeof(int) * 2 * kGenDepth, cudaHostAllocDefault) !=
-        cudaSuccess) {
-        s->hflag = nullptr;
-        return fail(h, PLSE_ENOMEM, "pinned host allocation");
-    }
+    s->hflag = pinned_slot_get();
+    if (!s->hflag) return fail(h, PLSE_ENOMEM, "pinned host allocation");
     s->cap_p = p;
     s->cap_gens = gens;
     s->tested_cap = cap;
@@ -322,6 +322,7 @@ int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uin
     Session &se = h->session;
     int rc = run_drain(h);
     if (rc) return rc;
+    StreamScope scope(h, st);
     se = Session();
     se.pop = pop;
     se.iters = iters;
@@ -333,7 +334,7 @@ int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uin
     const int ftarget = h->l == 1 ? 1 : 0;
     se.finished = (nv == 0 || nv <= ftarget || max_generations == 0);
     if (se.finished) return PLSE_OK;
-    rc = ensure_solver(h, pop, max_generations);
+    rc = ensure_solver(h, pop, max_generations, st);
     if (rc) return rc;
     SolverState *s = h->solver;
     const DevInst &I = h->di;
@@ -357,6 +358,17 @@ int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uin
     return PLSE_OK;
 }
 
+// Local search of the run: Partial-MPMA (greedy repair of each offspring, then
+// PartialCol) or the two-phase PLITS walk.  The automatic policy follows
+// Sec. 3.7: Partial-MPMA on highly constrained instances, r >= 0.8 of the cells
+// prefilled (exact integer test 5 * prefilled >= 4 * n^2).
+static bool partial_mpma(const plse_instance *h)
+{
+    const int mode = h->params.mode;
+    if (mode == PLSE_MODE_AUTO) return 5LL * h->nfixed >= 4LL * h->n * h->n;
+    return mode == PLSE_MODE_PARTIALCOL;
+}
+
 // Enqueues generation se.issued of the run on its stream without waiting for
 // anything: local search, best update, an 8-byte copy of (f*, done) to pinned
 // host memory, then Alg. 4, gather, matching and crossover.  If the bound is
@@ -375,9 +387,10 @@ static int issue_generation(plse_instance *h)
     const int slot = g % kGenDepth;
     const size_t PV = (size_t)p * nv, stride = (size_t)I.nw * I.nb;
     const int *skip = prm.stop_at_bound ? &s->ctrl->done : nullptr;
-    const int flags = prm.mode == PLSE_MODE_PARTIALCOL ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
-                                                       : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
+    const int flags = partial_mpma(h) ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
+                                      : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
     uint8_t *Pp = s->Pall[cur] + PV;
+    StreamScope scope(h, st);
     CK(cudaEventRecord(s->gev[slot][0], st));
     int rc = enqueue_local_search(h, s->SO, Pp, p, 0, g, se.iters, se.seed, flags, s->fprime, nullptr,
                                   s->wstats, st, skip);
@@ -483,6 +496,7 @@ int run_result(plse_instance *h, cudaStream_t st, int8_t *best_grid, int *best_s
     long long wst[7] = {0, 0, 0, 0, 0, 0, 0};
     if (h->solver && se.gen > 0) {
         SolverState *s = h->solver;
+        StreamScope scope(h, st);
         CK(cudaEventRecord(s->ev[3], st));
         Ctrl hctrl;
         CK(cudaMemcpyAsync(&hctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -530,11 +544,11 @@ int run_solve(plse_instance *h, int pop, int generations, int64_t iters, uint64_
     return rc;
 }
 
-int ensure_step_planes(plse_instance *h, size_t individuals)
+int ensure_step_planes(plse_instance *h, size_t individuals, cudaStream_t st)
 {
     const size_t need = individuals * (size_t)h->di.nw * h->di.nb;
     if (need <= h->step_planes_cap) return PLSE_OK;
-    int rc = dalloc(h, h->step_planes, need);
+    int rc = dalloc(h, h->step_planes, need, st);
     if (rc) return rc;
     h->step_planes_cap = need;
     return PLSE_OK;
@@ -607,11 +621,12 @@ int plse_distances(plse_handle h, const uint8_t *A, int na, const uint8_t *B, in
     if (na == 0 || nb == 0) return PLSE_OK;
     if (!D || (h->nv > 0 && (!A || !B))) return fail(h, PLSE_EINVAL, "plse_distances: null buffer");
     cudaStream_t st = (cudaStream_t)stream;
+    StreamScope scope(h, st);
     if (h->nv == 0) {
         CK(cudaMemsetAsync(D, 0, sizeof(int32_t) * (size_t)na * nb, st));
         return PLSE_OK;
     }
-    int rc = ensure_step_planes(h, (size_t)na + nb);
+    int rc = ensure_step_planes(h, (size_t)na + nb, st);
     if (rc) return rc;
     uint32_t *pa = h->step_planes, *pb = h->step_planes + (size_t)na * h->di.nw * h->di.nb;
     CK(launch_planes(h->di, A, na, pa, st));
@@ -626,9 +641,10 @@ int plse_pop_update(plse_handle h, int p, const uint8_t *Pall, const int64_t *e,
     if (!h || p < 1 || p > 65535 || !e || !sel || (h->nv > 0 && !Pall))
         return PLSE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = ensure_step_planes(h, 2 * (size_t)p);
+    StreamScope scope(h, st);
+    int rc = ensure_step_planes(h, 2 * (size_t)p, st);
     if (rc) return rc;
-    if ((rc = ensure_pop_scratch(h, h->step_ps, p))) return rc;
+    if ((rc = ensure_pop_scratch(h, h->step_ps, p, st))) return rc;
     if (h->nv > 0) CK(launch_planes(h->di, Pall, 2 * p, h->step_planes, st));
     CK(launch_pop_update(h->di, p, h->step_planes, e, h->params.spacing_gamma, h->step_ps, sel, filled,
                          nullptr, st));
@@ -642,7 +658,8 @@ int plse_matching(plse_handle h, int p, const uint8_t *P, const uint32_t *uid, u
         (h->nv > 0 && !P) || (h->params.matching == PLSE_MATCH_NEAREST && (!uid || !tested || !tcount)))
         return PLSE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = ensure_step_planes(h, (size_t)p);
+    StreamScope scope(h, st);
+    int rc = ensure_step_planes(h, (size_t)p, st);
     if (rc) return rc;
     if (h->nv > 0) CK(launch_planes(h->di, P, p, h->step_planes, st));
     CK(launch_matching(h->di, p, h->step_planes, uid, tested, tcount, h->params.tested_cap,

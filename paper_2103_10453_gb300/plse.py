@@ -20,7 +20,7 @@ PLSE_OK, PLSE_EINVAL, PLSE_ENOMEM, PLSE_ECUDA = 0, -1, -2, -3
 PLSE_EBUSY, PLSE_ECANCELLED, PLSE_ENOTSUP, PLSE_ECHECK = -4, -5, -6, -7
 PLSE_PENDING = 1
 LS_PHASE1, LS_PHASE2, LS_REPAIR, LS_PARTIALCOL = 1, 2, 4, 8
-MODE_PLITS, MODE_PARTIALCOL = 0, 1
+MODE_PLITS, MODE_PARTIALCOL, MODE_AUTO = 0, 1, 2
 MATCH_NEAREST, MATCH_RANDOM = 0, 1
 XOVER_AUX, XOVER_UX = 0, 1
 

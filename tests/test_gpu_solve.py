@@ -63,6 +63,16 @@ def test_partial_mpma_variant(plse, oracle_mod):
             oracle_params=oracle_mod.default_params(mode=1))
 
 
+@pytest.mark.parametrize("r, oracle_mode", [(0.8, 1), (0.85, 1), (0.79, 0), (0.5, 0)])
+def test_auto_mode_follows_the_fill_ratio(plse, oracle_mod, r, oracle_mode):
+    # Sec. 3.7: Partial-MPMA on instances with at least 80% of the cells prefilled
+    grid = inputs.random_insertion(20, r, 21)
+    assert (5 * int((grid != 0).sum()) >= 4 * 400) == (oracle_mode == 1)
+    compare(plse, oracle_mod, grid, 24, 4, 150, 8,
+            gpu_params=plse.default_params(mode=plse.MODE_AUTO),
+            oracle_params=oracle_mod.default_params(mode=oracle_mode))
+
+
 @pytest.mark.parametrize("variant", ["ux", "random"])
 def test_ablation_variants(plse, oracle_mod, variant):
     grid = inputs.random_insertion(15, 0.7, 5)
