@@ -66,6 +66,9 @@ def parse():
                     help="Latin square completion case: time to a complete square on "
                          "cyclic-delete instances, n in {50, 60, 70}, r in {0.3..0.8}")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--serve-walks", type=int, default=4,
+                    help="with --serve: cap on local-search walks per block (0 = automatic); a "
+                         "low cap leaves each SM room for other requests' short kernels")
     ap.add_argument("--serve-compare", action="store_true",
                     help="with --serve: also run the same jobs at once through plse_solve_batch")
     ap.add_argument("--rate", type=float, default=20.0)
@@ -477,6 +480,7 @@ def run_serve_case(args):
     arrivals = inputs.poisson_arrivals(args.requests, args.rate)
     inflight = args.inflight or 64
     srv = plse.Server(max_inflight=inflight, max_queue=args.requests)
+    srv.set_launch(0, args.serve_walks)
     # warm-up request (module load, first allocations), not counted
     w = srv.submit(inputs.tiny_n10(), 32, 2, 100, 1)
     srv.poll(w, wait_ms=-1)
@@ -513,7 +517,7 @@ def run_serve_case(args):
             key = "%d: %s" % (r["status"], r["detail"][:80])
             errors.setdefault(key, []).append(int(g.shape[0]))
     print(json.dumps({"case": "serve", "requests": args.requests, "rate_per_s": args.rate,
-                      "max_inflight": inflight, "generations": args.generations,
+                      "max_inflight": inflight, "walks_per_block_cap": args.serve_walks, "generations": args.generations,
                       "ok": ok, "wall_s": round(t_all, 3), "solves_per_s": round(ok / t_all, 3),
                       "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
                                      "p90": round(float(np.percentile(lat, 90)), 1),

@@ -226,6 +226,9 @@ int  plse_server_poll(plse_server s, int64_t ticket, int wait_ms, int8_t *best_g
                       plse_result *out);
 int  plse_server_cancel(plse_server s, int64_t ticket);
 int  plse_server_pending(plse_server s, int *queued, int *completed);
+/* Launch knobs (as plse_set_launch) for the handles of requests admitted from
+ * now on; they never change results. */
+int  plse_server_set_launch(plse_server s, int ls_warps, int ls_walks);
 void plse_server_destroy(plse_server s);
 
 /* ---- step entry points (device buffers, asynchronous on `stream`) ---------

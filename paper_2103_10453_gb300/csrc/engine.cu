@@ -197,6 +197,7 @@ struct plse_server_s {
 
     int device = 0;
     int max_inflight = 0, max_queue = 0;
+    int ls_warps = 0, ls_walks = 0;     // launch knobs applied to every request's handle
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request> queue;
@@ -290,6 +291,10 @@ struct plse_server_s {
                 plse_instance *h = nullptr;
                 int rc = plse_create(r.req.n, r.req.grid.data(), &h);
                 if (!rc) rc = plse_set_params(h, &r.req.params);
+                if (!rc) {
+                    std::lock_guard<std::mutex> lk(mu);
+                    rc = plse_set_launch(h, ls_warps, ls_walks);
+                }
                 if (!rc) rc = run_begin(h, r.req.job.pop, r.req.job.generations, r.req.job.iters, r.req.job.seed,
                                         streams[s]);
                 r.grid.assign((size_t)r.req.n * r.req.n, 0);
@@ -399,6 +404,15 @@ int plse_server_cancel(plse_server s, int64_t ticket)
         }
     if (s->done.count(ticket)) return PLSE_OK;   // already complete: nothing to cancel
     s->cancel_running[ticket] = true;
+    return PLSE_OK;
+}
+
+int plse_server_set_launch(plse_server s, int ls_warps, int ls_walks)
+{
+    if (!s || ls_warps < 0 || ls_walks < 0) return PLSE_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->ls_warps = ls_warps;
+    s->ls_walks = ls_walks;
     return PLSE_OK;
 }
 

@@ -820,6 +820,28 @@ __device__ __forceinline__ void list_append(const Ctx &c, bool want, int u, int 
     len += __popc(b);
 }
 
+// One scan pass of a one-warp walk over list entries base .. base+31: stale
+// entries (no longer candidates) are dropped and lose their membership bit, live
+// ones are written back contiguously at wpos, so the list stays about as long as
+// the candidate set and a scan needs no pass over stale entries.  Returns the
+// lane's live vertex or -1.
+__device__ __forceinline__ int list_pass(const Ctx &c, int base, int len, int &wpos)
+{
+    const int qq = base + c.lane;
+    int v = -1;
+    bool lv = false;
+    if (qq < len) {
+        v = c.s.list[qq];
+        lv = (c.s.cmask[v >> 5] >> (v & 31)) & 1u;
+        if (!lv) atomicAnd(&c.s.lmask[v >> 5], ~(1u << (v & 31)));
+    }
+    const uint32_t b = __ballot_sync(FULL, lv);
+    __syncwarp();                                     // every entry of the pass read before any write
+    if (lv) c.s.list[wpos + __popc(b & ((1u << c.lane) - 1u))] = (uint16_t)v;
+    wpos += __popc(b);
+    return lv ? v : -1;
+}
+
 // ---- PLITS phase (Alg. 3 with phi2 = 2*phi) --------------------------------
 template <int NWC, int NW>
 __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, const Ctx &c, uint32_t *G, uint8_t *gbest,
@@ -869,9 +891,7 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         const bool low = c.s.scal[2] == 0;            // every count <= 3
         unsigned long long key = kNoKey;
         int live = 0;
-        for (int qq = c.gt; qq < len; qq += 32 * NW) {
-            const int v = c.s.list[qq];
-            if (!((c.s.cmask[v >> 5] >> (v & 31)) & 1u)) continue;   // stale entry
+        auto consider = [&](int v) {
             ++live;
             int pairs;
             bool slow = true;
@@ -880,6 +900,21 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             if (slow) kv = eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs);
             st.pairs += pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, c.s.S[v]));
+        };
+        if constexpr (NW == 1) {
+            int wpos = 0;
+            for (int base = 0; base < len; base += 32) {
+                const int v = list_pass(c, base, len, wpos);
+                if (v >= 0) consider(v);
+            }
+            if (c.lane == 0) c.s.scal[0] = wpos;
+            __syncwarp();
+            len = wpos;
+        } else {
+            for (int qq = c.gt; qq < len; qq += 32 * NW) {
+                const int v = c.s.list[qq];
+                if ((c.s.cmask[v >> 5] >> (v & 31)) & 1u) consider(v);   // else a stale entry
+            }
         }
         int ncand;
         const unsigned long long best = group_best<NW>(c, (int)(t & 1), key, live, ncand);
@@ -1070,9 +1105,7 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         const bool low = c.s.scal[2] == 0;            // every count <= 3
         unsigned long long key = kNoKey;
         int live = 0;
-        for (int qq = c.gt; qq < len; qq += 32 * NW) {
-            const int v = c.s.list[qq];
-            if (!((c.s.cmask[v >> 5] >> (v & 31)) & 1u)) continue;
+        auto consider = [&](int v) {
             ++live;
             int pairs;
             bool slow = true;
@@ -1081,6 +1114,21 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
             if (slow) kv = eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs);
             st.pairs += pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, 0));
+        };
+        if constexpr (NW == 1) {
+            int wpos = 0;
+            for (int base = 0; base < len; base += 32) {
+                const int v = list_pass(c, base, len, wpos);
+                if (v >= 0) consider(v);
+            }
+            if (c.lane == 0) c.s.scal[0] = wpos;
+            __syncwarp();
+            len = wpos;
+        } else {
+            for (int qq = c.gt; qq < len; qq += 32 * NW) {
+                const int v = c.s.list[qq];
+                if ((c.s.cmask[v >> 5] >> (v & 31)) & 1u) consider(v);
+            }
         }
         int ncand;
         const unsigned long long best = group_best<NW>(c, (int)(t & 1), key, live, ncand);

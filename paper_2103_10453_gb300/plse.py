@@ -103,6 +103,7 @@ SIGNATURES = {
     "plse_server_poll": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, C.POINTER(Result)]),
     "plse_server_cancel": (C.c_int, [_vp, C.c_int64]),
     "plse_server_pending": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "plse_server_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "plse_server_destroy": (None, [_vp]),
     "plse_init_population": (C.c_int, [_vp, C.c_int, _u64, _vp, _vp]),
     "plse_local_search": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _i64, _u64, C.c_int,
@@ -370,6 +371,11 @@ class Server:
         rc = self.lib.plse_server_cancel(self.h, ticket)
         if rc != PLSE_OK:
             raise PlseError(rc, "plse_server_cancel")
+
+    def set_launch(self, ls_warps=0, ls_walks=0):
+        rc = self.lib.plse_server_set_launch(self.h, ls_warps, ls_walks)
+        if rc != PLSE_OK:
+            raise PlseError(rc, "plse_server_set_launch")
 
     def pending(self):
         q, c = C.c_int(), C.c_int()
