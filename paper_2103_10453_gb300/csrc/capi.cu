@@ -239,6 +239,8 @@ int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
     if (rc) return rc;
     rc = grow(h, ws.LIST, ws.LIST_cap, (size_t)slots * h->di.nv, false, st); // rebuilt by every phase
     if (rc) return rc;
+    rc = grow(h, ws.XR, ws.XR_cap, (size_t)slots * 2 * h->di.n * h->di.n1p, false, st);   // idem
+    if (rc) return rc;
     rc = grow(h, ws.slot_clock, ws.clock_cap, (size_t)slots, true, st);
     if (rc) return rc;
     return grow(h, ws.counters, ws.counters_cap, 8, true, st);
@@ -280,6 +282,7 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.G = h->ws.G;
     a.TC = h->ws.TC;
     a.LIST = h->ws.LIST;
+    a.XR = h->ws.XR;
     a.slot_clock = h->ws.slot_clock;
     a.work_counter = h->ws.counters;
     a.error_flag = h->ws.counters + 1;
@@ -363,6 +366,7 @@ void plse_destroy(plse_handle h)
     dev_free(ws.G, st);
     dev_free(ws.TC, st);
     dev_free(ws.LIST, st);
+    dev_free(ws.XR, st);
     dev_free(ws.slot_clock, st);
     dev_free(ws.counters, st);
     if (h->done_ev) cudaEventDestroy(h->done_ev);

@@ -98,6 +98,7 @@ struct Slot {
     uint32_t *cmask;            // candidate bitmask [nw]
     uint32_t *lmask;            // vertices present in the candidate list [nw]
     uint16_t *list;             // candidate list (may hold stale entries) [nv], global memory
+    uint16_t *xr;               // [2n][n1p] XOR of the ids of a line's vertices of each colour, global
     uint2 *tc;                  // tabu cache [nv] in global memory (L1-resident for the candidates):
                                 // x = e0 | e1 << 16, y = c0 | c1 << 8 | emax << 16
     unsigned long long *red;    // [2][NW] best key per warp (double-buffered)
@@ -141,6 +142,7 @@ __device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I)
     c.s.cmask = reinterpret_cast<uint32_t *>(sb + p.off_cmask);
     c.s.lmask = reinterpret_cast<uint32_t *>(sb + p.off_lmask);
     c.s.list = nullptr;         // set once the walk slot is known
+    c.s.xr = nullptr;
     c.s.tc = nullptr;           // set once the walk slot is known
     c.s.red = reinterpret_cast<unsigned long long *>(sb + p.off_red);
     c.s.red_cnt = reinterpret_cast<int *>(sb + p.off_red + 16 * NW);
@@ -233,6 +235,39 @@ __device__ __forceinline__ int count_step(uint32_t *P, int cw, int line, int k, 
     return new_hi - old_hi;
 }
 
+// count of colour k from the seven plane words of its 32-colour word
+__device__ __forceinline__ int count_in(const uint32_t (&x)[7], int k)
+{
+    const uint32_t b = k & 31;
+    int c = 0;
+#pragma unroll
+    for (int p = 0; p < 7; ++p) c |= (int)((x[p] >> b) & 1u) << p;
+    return c;
+}
+
+// count_step that also returns the updated plane words in x
+__device__ __forceinline__ int count_step_words(uint32_t *P, int cw, int line, int k, bool inc, uint32_t (&xo)[7])
+{
+    uint4 *w = reinterpret_cast<uint4 *>(P + ((size_t)line * cw + (k >> 5)) * kPlanes);
+    uint4 a = w[0], b = w[1];
+    uint32_t x[7] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+    const uint32_t bit = 1u << (k & 31);
+    const int old_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
+    uint32_t carry = bit;
+#pragma unroll
+    for (int p = 0; p < 7; ++p) {
+        const uint32_t t = inc ? (x[p] & carry) : (~x[p] & carry);
+        x[p] ^= carry;
+        carry = t;
+    }
+    w[0] = make_uint4(x[0], x[1], x[2], x[3]);
+    w[1] = make_uint4(x[4], x[5], x[6], b.w);
+#pragma unroll
+    for (int p = 0; p < 7; ++p) xo[p] = x[p];
+    const int new_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
+    return new_hi - old_hi;
+}
+
 __device__ __forceinline__ int count_of(const uint32_t *P, int cw, int line, int k)
 {
     const uint32_t *w = P + ((size_t)line * cw + (k >> 5)) * kPlanes;
@@ -264,9 +299,15 @@ __device__ __forceinline__ void build_planes(const DevInst &I, const Ctx &c)
         const int32_t *ptr = col ? I.col_ptr : I.row_ptr;
         const uint16_t *lst = col ? I.col_v : I.row_v;
         uint32_t *T = col ? c.s.KP : c.s.RP;
+        uint16_t *X = c.s.xr + (size_t)l * I.n1p;
+        for (int k = 0; k < I.n1p; ++k) X[k] = 0;
         for (int q = __ldg(&ptr[line]); q < __ldg(&ptr[line + 1]); ++q) {
-            const int k = c.s.S[__ldg(&lst[q])];
-            if (k) count_step(T, c.cw, line, k, true);
+            const int u = __ldg(&lst[q]);
+            const int k = c.s.S[u];
+            if (k) {
+                count_step(T, c.cw, line, k, true);
+                X[k] ^= (uint16_t)u;
+            }
         }
     }
     gsync<NW>(c);
@@ -937,71 +978,64 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             // lanes 2-3 the same for colour j (folded into lanes 0-1 when i and j
             // share a 32-colour word, so that no two lanes touch one plane word)
             const bool same = i && j && ((i >> 5) == (j >> 5));
+            // member-id XOR of (row r | column cc, colour i | j), read first so that
+            // its latency overlaps the count updates: lane 0 row/i, 1 column/i,
+            // 2 row/j, 3 column/j
+            const int xk = c.lane < 2 ? i : j;
+            const size_t xidx = (size_t)((c.lane & 1) ? I.n + cc : r) * I.n1p + xk;
+            const int xold = (c.lane < 4 && xk) ? (int)c.s.xr[xidx] : 0;
+            int cnt_i = 0, cnt_j = 0;
             if (c.lane < 4) {
                 uint32_t *P = (c.lane & 1) ? c.s.KP : c.s.RP;
                 const int line = (c.lane & 1) ? cc : r;
                 int dh = 0;
+                uint32_t w[7];
                 if (c.lane < 2) {
-                    if (i) dh += count_step(P, c.cw, line, i, false);
-                    if (same) dh += count_step(P, c.cw, line, j, true);
+                    if (i) dh += count_step_words(P, c.cw, line, i, false, w);
+                    if (same) dh += count_step_words(P, c.cw, line, j, true, w);
+                    if (i) cnt_i = count_in(w, i);       // counts after the move
+                    if (same) cnt_j = count_in(w, j);
                 } else if (j && !same) {
-                    dh += count_step(P, c.cw, line, j, true);
+                    dh += count_step_words(P, c.cw, line, j, true, w);
+                    cnt_j = count_in(w, j);
                 }
                 if (dh) atomicAdd(&c.s.scal[2], dh);
                 if (c.lane == 0) c.s.S[v] = (uint8_t)j;
+                if (xk) c.s.xr[xidx] = (uint16_t)(xold ^ v);   // v leaves i, joins j
             }
-            __syncwarp();
             // counts of colours i and j on the moved row and column, after the move
-            const int Ri = i ? count_of(c.s.RP, c.cw, r, i) : 0, Rj = j ? count_of(c.s.RP, c.cw, r, j) : 0;
-            const int Ki = i ? count_of(c.s.KP, c.cw, cc, i) : 0, Kj = j ? count_of(c.s.KP, c.cw, cc, j) : 0;
-            // Conflict status of a mate u can only change if it is the only other
-            // member of the line with colour i (count after the move == 1) or with
-            // colour j (count after == 2): lines where neither holds are skipped.
-            const bool need_r = (i && Ri == 1) || (j && Rj == 2);
-            const bool need_c = (i && Ki == 1) || (j && Kj == 2);
-            int rb = 0, re = 0, cb = 0, ce = 0;
-            if (need_r) { rb = __ldg(&I.row_ptr[r]); re = __ldg(&I.row_ptr[r + 1]); }
-            if (need_c) { cb = __ldg(&I.col_ptr[cc]); ce = __ldg(&I.col_ptr[cc + 1]); }
+            const int Ri = __shfl_sync(FULL, cnt_i, 0), Ki = __shfl_sync(FULL, cnt_i, 1);
+            const int Rj = __shfl_sync(FULL, cnt_j, same ? 0 : 2), Kj = __shfl_sync(FULL, cnt_j, same ? 1 : 3);
+            __syncwarp();
+            // The mates whose conflict status can change, one per (line, colour) at
+            // most: the only other holder of colour i (count after the move 1) and
+            // the other holder of colour j (count after 2).  Each is read from the
+            // member-id XOR of its line: lane 0 row/i, 1 column/i, 2 row/j, 3 column/j.
             int dconf = 0;
-            const int span_len = max(re - rb, ce - cb);
-            for (int b0 = 0; b0 < span_len; b0 += 32) {
-                const int qr = rb + b0 + c.lane, qc = cb + b0 + c.lane;
-                int ur = -1, uc = -1;
-                if (qr < re) {
-                    const int u = __ldg(&I.row_v[qr]);
-                    const int su = c.s.S[u];
-                    if (u != v && su != 0 && (su == i || su == j)) ur = u | (su << 16);
-                }
-                if (qc < ce) {
-                    const int u = __ldg(&I.col_v[qc]);
-                    const int su = c.s.S[u];
-                    if (u != v && su != 0 && (su == i || su == j)) uc = u | (su << 16);
-                }
-                if (!__any_sync(FULL, ur >= 0 || uc >= 0)) continue;
-                bool wr = false, wc = false;
-                if (ur >= 0) {                           // row-mate: its row count is Ri / Rj
-                    const int u = ur & 0xFFFF, su = ur >> 16;
-                    const int g = (su == i ? Ri : Rj) + count_of(c.s.KP, c.cw, c.rc[u] & 255, su) - 2;
+            int u = -1, su = 0, cl = 0;
+            const bool row_mate = (c.lane & 1) == 0;
+            if (c.lane == 0 && i && Ri == 1) { u = xold ^ v; su = i; cl = Ri; }   // the last holder of i
+            if (c.lane == 1 && i && Ki == 1) { u = xold ^ v; su = i; cl = Ki; }
+            if (c.lane == 2 && j && Rj == 2) { u = xold; su = j; cl = Rj; }       // the other holder of j
+            if (c.lane == 3 && j && Kj == 2) { u = xold; su = j; cl = Kj; }
+            bool want = false, bad_mate = false;
+            if (u >= 0) {
+                if (u >= I.nv || u == v || c.s.S[u] != su) {
+                    bad_mate = true;                     // inconsistent table: report, touch nothing
+                } else {
+                    const uint16_t urc = c.rc[u];
+                    const int g = cl + (row_mate ? count_of(c.s.KP, c.cw, urc & 255, su)
+                                                 : count_of(c.s.RP, c.cw, urc >> 8, su)) - 2;
                     const int nc = g > 0, oc = (c.s.cmask[u >> 5] >> (u & 31)) & 1;
                     if (nc != oc) {
                         atomicXor(&c.s.cmask[u >> 5], 1u << (u & 31));
                         dconf += nc - oc;
-                        wr = nc && !((c.s.lmask[u >> 5] >> (u & 31)) & 1u);
+                        want = nc && !((c.s.lmask[u >> 5] >> (u & 31)) & 1u);
                     }
                 }
-                if (uc >= 0) {                           // column-mate: its column count is Ki / Kj
-                    const int u = uc & 0xFFFF, su = uc >> 16;
-                    const int g = (su == i ? Ki : Kj) + count_of(c.s.RP, c.cw, c.rc[u] >> 8, su) - 2;
-                    const int nc = g > 0, oc = (c.s.cmask[u >> 5] >> (u & 31)) & 1;
-                    if (nc != oc) {
-                        atomicXor(&c.s.cmask[u >> 5], 1u << (u & 31));
-                        dconf += nc - oc;
-                        wc = nc && !((c.s.lmask[u >> 5] >> (u & 31)) & 1u);
-                    }
-                }
-                list_append(c, wr, ur & 0xFFFF, len);
-                list_append(c, wc, uc & 0xFFFF, len);
             }
+            list_append(c, want, u, len);
+            const bool any_bad = __any_sync(FULL, bad_mate);
             if (c.lane == 0) {
                 const int newc = j ? (int)(Rj + Kj - 2 > 0) : 0;
                 if (j != 0 && !newc) atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
@@ -1014,9 +1048,11 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
                 tabu_insert(I, c, G, ck, v, i, trel + (uint32_t)T);
                 c.s.scal[4] = nconf + dconf;
                 c.s.scal[0] = len;
+                c.s.scal[6] = any_bad ? 1 : 0;
             }
         }
         gsync<NW>(c);
+        if (c.s.scal[6]) { ok = false; break; }
         nconf = c.s.scal[4];
         st.moves += 1;
         if (c.gt == 0) st.deg += vertex_degree(I, c, v);
@@ -1231,6 +1267,7 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
     uint32_t *G = a.G + (size_t)slot * I.nv * I.n1p;
     c.s.tc = a.TC + (size_t)slot * I.nv;
     c.s.list = a.LIST + (size_t)slot * I.nv;
+    c.s.xr = a.XR + (size_t)slot * 2 * I.n * I.n1p;
 
     for (;;) {
         if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);

@@ -8,8 +8,8 @@
 // loop that must not hit the implicit device-wide synchronisation of
 // cudaMalloc / cudaFree.  This entry point serves them: it calls no cudaMalloc,
 // cudaFree or allocating library routine.  Its scratch (the evicted-tabu
-// tables, the tabu caches, the candidate lists, the per-slot clocks, the walk
-// counter and the check flag) lives in
+// tables, the tabu caches, the candidate lists, the member-id XOR tables, the
+// per-slot clocks, the walk counter and the check flag) lives in
 // the file-scope array below, kNoAllocScratchBytes bytes on every GPU that loads
 // the library, held until the process exits.
 //
@@ -82,9 +82,11 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     if (rc) return rc;
 
     // walk slots that fit: each needs an evicted-tabu table (4 * |V| * n1p bytes),
-    // a tabu cache (8 * |V| bytes), a candidate list (2 * |V| bytes) and a clock word
-    const size_t table_bytes = 4 * (size_t)h->di.nv * h->di.n1p + 10 * (size_t)h->di.nv;
-    const size_t max_slots = (kNoAllocScratchBytes - kCounterBytes - 1024) / (table_bytes + 4);   // 1024: alignment
+    // a tabu cache (8 * |V| bytes), a candidate list (2 * |V| bytes), a member-id
+    // XOR table (4 * n * n1p bytes) and a clock word
+    const size_t xr_bytes = 4 * (size_t)h->di.n * h->di.n1p;
+    const size_t table_bytes = 4 * (size_t)h->di.nv * h->di.n1p + 10 * (size_t)h->di.nv + xr_bytes;
+    const size_t max_slots = (kNoAllocScratchBytes - kCounterBytes - 1280) / (table_bytes + 4);   // 1280: alignment
     if (max_slots < 1)
         return fail(h, PLSE_ENOTSUP,
                     "plse_local_search_noalloc: one walk slot needs %zu bytes of scratch, more than the %zu "
@@ -100,8 +102,8 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
         if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: no walk slot fits");
     }
     const size_t slots = (size_t)L.slots();
-    // layout: [counters][slot clocks][evicted-tabu tables][tabu caches][lists];
-    // the first three must start at zero, caches and lists are reset by every phase
+    // layout: [counters][slot clocks][evicted-tabu tables][tabu caches][lists][XOR
+    // tables]; the first three must start at zero, the rest is rebuilt by every phase
     int *counters = reinterpret_cast<int *>(scratch);
     uint32_t *clocks = reinterpret_cast<uint32_t *>(scratch + kCounterBytes);
     const size_t tables_off = (kCounterBytes + 4 * slots + 255) & ~size_t(255);
@@ -110,7 +112,9 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     uint2 *tcache = reinterpret_cast<uint2 *>(scratch + tc_off);
     const size_t list_off = (tc_off + slots * 8 * (size_t)h->di.nv + 255) & ~size_t(255);
     uint16_t *lists = reinterpret_cast<uint16_t *>(scratch + list_off);
-    const size_t used = list_off + slots * 2 * (size_t)h->di.nv;
+    const size_t xr_off = (list_off + slots * 2 * (size_t)h->di.nv + 255) & ~size_t(255);
+    uint16_t *xrs = reinterpret_cast<uint16_t *>(scratch + xr_off);
+    const size_t used = xr_off + slots * xr_bytes;
     if (used > kNoAllocScratchBytes) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: scratch overflow");
     e = cudaMemsetAsync(scratch, 0, tc_off, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "plse_local_search_noalloc: clear scratch");
@@ -142,6 +146,7 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     a.G = tables;
     a.TC = tcache;
     a.LIST = lists;
+    a.XR = xrs;
     a.slot_clock = clocks;
     a.work_counter = counters;
     a.error_flag = counters + 1;

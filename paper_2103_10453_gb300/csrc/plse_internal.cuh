@@ -57,6 +57,7 @@ struct LSArgs {
     uint32_t *G;                  // [slots][nv * n1p] evicted tabu expiries (absolute clock)
     uint2 *TC;                    // [slots][nv] two-entry tabu caches (relative clock)
     uint16_t *LIST;               // [slots][nv] candidate lists
+    uint16_t *XR;                 // [slots][2n][n1p] member-id XOR per line and colour
     uint32_t *slot_clock;         // [slots] next free clock value of each slot
     int *work_counter;            // dynamic walk scheduler, zeroed before launch
     int *error_flag;              // nonzero after a failed device bound check
