@@ -667,17 +667,20 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
     bool has0 = (i != 0);
     int best = INT_MAX;
 #pragma unroll
+    // a cached colour whose tabu has expired is an ordinary admissible colour
+    // and stays in m; a still-tabu one is taken out and admitted by aspiration only
     for (int sx = 0; sx < 2; ++sx) {
         const uint32_t cs = sx ? c1 : c0, es = sx ? e1 : e0;
+        if (es < trel) continue;
         if (cs == 0u) {
             if (has0) {
                 has0 = false;
-                if (es < trel || d2zero < A) best = min(best, d2zero * kKeyScale);
+                if (d2zero < A) best = min(best, d2zero * kKeyScale);
             }
         } else if (cs < 128u && test_bit<NWC>(m, cs)) {
             clear_bit<NWC>(m, cs);
             const int d2 = base2 + mult * value3<NWC>(s0, s1, s2, cs);
-            if (es < trel || d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
+            if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
         }
     }
     if (has0) best = min(best, d2zero * kKeyScale);
@@ -739,15 +742,16 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
 #pragma unroll
         for (int sx = 0; sx < 2; ++sx) {
             const uint32_t cs = sx ? c1 : c0, es = sx ? e1 : e0;
+            if (es < trel) continue;                  // expired: stays in m
             if (cs == 0u) {
                 if (has0) {
                     has0 = false;
-                    if (es < trel || d2zero < A) best = min(best, d2zero * kKeyScale);
+                    if (d2zero < A) best = min(best, d2zero * kKeyScale);
                 }
             } else if (cs < 128u && test_bit<NWC>(m, cs)) {
                 clear_bit<NWC>(m, cs);
                 const int d2 = base2 + mult * (count_of(c.s.RP, NWC, r, (int)cs) + count_of(c.s.KP, NWC, cc, (int)cs));
-                if (es < trel || d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
+                if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
             }
         }
         if (has0) best = min(best, d2zero * kKeyScale);
