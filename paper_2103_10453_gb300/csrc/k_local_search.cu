@@ -882,7 +882,8 @@ __device__ __forceinline__ int list_pass(const Ctx &c, int base, int len, int &w
     }
     const uint32_t b = __ballot_sync(FULL, lv);
     __syncwarp();                                     // every entry of the pass read before any write
-    if (lv) c.s.list[wpos + __popc(b & ((1u << c.lane) - 1u))] = (uint16_t)v;
+    const int to = wpos + __popc(b & ((1u << c.lane) - 1u));
+    if (lv && to != qq) c.s.list[to] = (uint16_t)v;  // entries that do not move stay cached
     wpos += __popc(b);
     return lv ? v : -1;
 }
