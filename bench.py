@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--lsc", action="store_true",
                     help="Latin square completion case: time to a complete square on "
                          "cyclic-delete instances, n in {50, 60, 70}, r in {0.3..0.8}")
+    ap.add_argument("--dist-case", action="store_true",
+                    help="distance kernel case: plse_distances on --pop x --pop colourings of the "
+                         "n=70, r=0.3 instance, ALU roofline")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--serve-walks", type=int, default=4,
                     help="with --serve: cap on local-search walks per block (0 = automatic); a "
@@ -155,12 +158,11 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-# DRAM bytes per tabu move of local_search_kernel, from one ncu capture of the
-# small steady case (bench.py --ls-case 0.3 --pop 1216 --ls-iters 3000):
-# dram__bytes_read.sum + dram__bytes_write.sum = 17.75 MB for 1.8116e6 moves.
-# Scaled to a benchmark launch by its moves; the counters belong to the kernel
-# as captured, so this is None whenever the kernel has changed since.
-LS_DRAM_BYTES_PER_MOVE = 17.75e6 / 1.8116e6
+# DRAM bytes per tabu move of local_search_kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a launch with walks as long
+# as the benchmark's; scaled to a benchmark launch by its moves.  None whenever
+# the kernel has changed since the capture.
+LS_DRAM_BYTES_PER_MOVE = None
 
 
 def walk_bytes(w):
@@ -256,8 +258,8 @@ def run_gpu(args):
                 "frac": round(achieved / smem_peak, 4) if achieved else None,
                 "traffic": (round(LS_DRAM_BYTES_PER_MOVE * wdelta["moves"] / launches_ls)
                             if LS_DRAM_BYTES_PER_MOVE else None),
-                "traffic_note": "DRAM bytes per launch scaled by moves from the ncu capture of the "
-                                "small steady case (profiles/)",
+                "traffic_note": "DRAM bytes per launch, scaled by moves from an ncu capture of a launch "
+                                "with benchmark-length walks (profiles/)",
                 "kernel": "local_search_kernel",
                 "peak_source": "derived: %d SMs x 128 B/clk x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
                                % (sm_count, sm_max),
@@ -584,6 +586,49 @@ def run_lsc_case(args):
                       "rows": rows}), flush=True)
 
 
+def run_dist_case(args):
+    """Hamming distances (Sec. 3.4) between two sets of --pop random colourings
+    of the n=70, r=0.3 instance through plse_distances (bit planes, then the 64 x
+    64 tile kernel); --steps timed launches after a warm-up one, CUDA events on
+    the launching stream.  ALU roofline: per (pair, 32-vertex word) the kernel
+    does nb XORs, nb - 1 ORs, one popcount and one add (2 nb + 1 integer
+    operations), against SMs x 128 lanes x the maximum SM clock."""
+    import torch
+    from paper_2103_10453_gb300 import inputs, plse
+    G = plse.Instance(inputs.n70(0.3))
+    p = args.pop
+    A = torch.empty((p, G.nv), dtype=torch.uint8, device="cuda")
+    B = torch.empty_like(A)
+    G.init_population(p, 1, A)
+    G.init_population(p, 2, B)
+    D = torch.empty((p, p), dtype=torch.int32, device="cuda")
+    G.distances(A, p, B, p, D)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(args.steps, 1)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.distances(A, p, B, p, D)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    nw, nb = (G.nv + 31) // 32, 7
+    t = statistics.median(ms) / 1e3
+    ops = float(p) * p * nw * (2 * nb + 1)
+    peaks = measured_peaks()
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sm * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    print(json.dumps({"case": "distances", "n": 70, "r": 0.3, "nv": G.nv, "pairs": p * p,
+                      "ms": round(statistics.median(ms), 3),
+                      "pair_words_per_s": round(p * p * nw / t, 1),
+                      "roofline": {"bound": "alu", "achieved": round(ops / t / 1e12, 3),
+                                   "peak": round(peak / 1e12, 3), "unit": "Tops/s",
+                                   "frac": round(ops / t / peak, 4),
+                                   "peak_source": "derived: %d SMs x 128 lanes x max SM clock" % sm,
+                                   "note": "includes the bit-plane pass over both sets"}}), flush=True)
+    G.close()
+
+
 def main():
     args = parse()
     if args.ls_case is not None:
@@ -596,6 +641,8 @@ def main():
         run_pop_sweep(args)
     elif args.lsc:
         run_lsc_case(args)
+    elif args.dist_case:
+        run_dist_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
