@@ -631,11 +631,9 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
                                                uint32_t trel, int v, int mult, int base_unc, int A, int &pairs,
                                                bool &slow)
 {
+    // the tabu-cache entry (global memory) is loaded first and used last, so its
+    // latency overlaps the shared-memory loads and the bit-sliced arithmetic
     const uint2 te = c.s.tc[v];
-    const uint32_t e0 = te.x & 0xFFFFu, e1 = te.x >> 16;
-    const uint32_t c0 = te.y & 0xFFu, c1 = (te.y >> 8) & 0xFFu, em = te.y >> 16;
-    slow = em >= trel;
-    if (slow) return INT_MAX;
     const int i = c.s.S[v];
     const uint16_t rc = c.rc[v];
     const int r = rc >> 8, cc = rc & 255;
@@ -666,6 +664,10 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
     if (i) clear_bit<NWC>(m, (uint32_t)i);
     bool has0 = (i != 0);
     int best = INT_MAX;
+    const uint32_t e0 = te.x & 0xFFFFu, e1 = te.x >> 16;
+    const uint32_t c0 = te.y & 0xFFu, c1 = (te.y >> 8) & 0xFFu, em = te.y >> 16;
+    slow = em >= trel;                        // evicted entries may apply: full evaluation
+    if (slow) return INT_MAX;
 #pragma unroll
     // a cached colour whose tabu has expired is an ordinary admissible colour
     // and stays in m; a still-tabu one is taken out and admitted by aspiration only
