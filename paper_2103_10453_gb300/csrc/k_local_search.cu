@@ -77,7 +77,7 @@ __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
 {
     const int cw = colour_words(I.n);
     SmemPlan p;
-    p.inst = align16(align16(2 * (size_t)I.nv) + 32 * (size_t)I.n);
+    p.inst = align16(align16(2 * (size_t)I.nv) + 32 * (size_t)I.n + 2 * (size_t)I.n);
     size_t o = 0;
     p.off_S = o;      o = align16(o + (size_t)I.nv);
     p.off_RP = o;     o += 32 * (size_t)I.n * cw;
@@ -110,6 +110,7 @@ struct Slot {
 struct Ctx {
     const uint16_t *rc;         // [nv] row << 8 | column (shared by the block)
     const uint4 *allow;         // [2n] allowed colours per row, then per column (shared)
+    const uint8_t *linelen;     // [2n] reduced vertices per row, then per column (shared)
     Slot s;
     int cw;                     // colour words of the plane layout
     int g;                      // group (walk slot) within the block
@@ -131,6 +132,7 @@ __device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I)
     Ctx c;
     c.rc = reinterpret_cast<const uint16_t *>(base);
     c.allow = reinterpret_cast<const uint4 *>(base + align16(2 * (size_t)I.nv));
+    c.linelen = base + align16(2 * (size_t)I.nv) + 32 * (size_t)I.n;
     c.g = threadIdx.x / (32 * NW);
     c.gt = threadIdx.x % (32 * NW);
     c.lane = threadIdx.x & 31;
@@ -786,9 +788,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
 __device__ __forceinline__ int vertex_degree(const DevInst &I, const Ctx &c, int v)
 {
     const uint16_t rc = c.rc[v];
-    const int r = rc >> 8, cc = rc & 255;
-    return (__ldg(&I.row_ptr[r + 1]) - __ldg(&I.row_ptr[r]) - 1) +
-           (__ldg(&I.col_ptr[cc + 1]) - __ldg(&I.col_ptr[cc]) - 1);
+    return (int)c.linelen[rc >> 8] + (int)c.linelen[I.n + (rc & 255)] - 2;
 }
 
 // reserve a clock range for one phase of this slot
@@ -1265,7 +1265,11 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
     uint16_t *rc_s = reinterpret_cast<uint16_t *>(smem);
     uint4 *allow_s = reinterpret_cast<uint4 *>(smem + align16(2 * (size_t)I.nv));
     for (int v = threadIdx.x; v < I.nv; v += blockDim.x) rc_s[v] = __ldg(&I.rc[v]);
-    for (int r = threadIdx.x; r < 2 * I.n; r += blockDim.x) allow_s[r] = r < I.n ? I.allow_row[r] : I.allow_col[r - I.n];
+    uint8_t *len_s = smem + align16(2 * (size_t)I.nv) + 32 * (size_t)I.n;
+    for (int r = threadIdx.x; r < 2 * I.n; r += blockDim.x) {
+        allow_s[r] = r < I.n ? I.allow_row[r] : I.allow_col[r - I.n];
+        len_s[r] = (uint8_t)(r < I.n ? I.row_ptr[r + 1] - I.row_ptr[r] : I.col_ptr[r - I.n + 1] - I.col_ptr[r - I.n]);
+    }
     __syncthreads();
 
     Ctx c = make_ctx<NW>(smem, I);

@@ -65,6 +65,13 @@ struct TileSmem {
     uint32_t B[kWC][NB][kTile];
 };
 
+// Row swizzle of a staged (word, plane) slot: consecutive staging threads write
+// one row of 56 consecutive slots, 64 words apart, which would all fall in one
+// bank; XOR-ing the row with a multiple of 4 that depends on the slot spreads
+// them over 16 banks and keeps every aligned group of 4 rows contiguous (the
+// 16-byte row reads stay aligned).
+__device__ __forceinline__ int tile_swz(int slot) { return (slot & 15) << 2; }
+
 // Distances between rows ra[0..63] and columns cb[0..63] (indices into the
 // plane array; -1 = padding) accumulated into acc[4][4].
 template <int NB>
@@ -92,8 +99,9 @@ __device__ __forceinline__ void tile_distances(const uint32_t *__restrict__ plan
                 if (xa >= 0) va = __ldg(planesA + (size_t)xa * stride + (size_t)(w0 + wq) * NB + b);
                 if (xb >= 0) vb = __ldg(planesB + (size_t)xb * stride + (size_t)(w0 + wq) * NB + b);
             }
-            sm.A[wq][b][r] = va;
-            sm.B[wq][b][r] = vb;
+            const int rs = r ^ tile_swz(wq * NB + b);
+            sm.A[wq][b][rs] = va;
+            sm.B[wq][b][rs] = vb;
         }
         __syncthreads();
         for (int wq = 0; wq < wc; ++wq) {
@@ -107,8 +115,9 @@ __device__ __forceinline__ void tile_distances(const uint32_t *__restrict__ plan
                 for (int b = 0; b < 4; ++b) o[a][b] = 0u;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                const uint4 xa = *reinterpret_cast<const uint4 *>(&sm.A[wq][b][4 * ty]);
-                const uint4 yb = *reinterpret_cast<const uint4 *>(&sm.B[wq][b][4 * tx]);
+                const int sw = tile_swz(wq * NB + b);
+                const uint4 xa = *reinterpret_cast<const uint4 *>(&sm.A[wq][b][(4 * ty) ^ sw]);
+                const uint4 yb = *reinterpret_cast<const uint4 *>(&sm.B[wq][b][(4 * tx) ^ sw]);
                 x[0] = xa.x; x[1] = xa.y; x[2] = xa.z; x[3] = xa.w;
                 y[0] = yb.x; y[1] = yb.y; y[2] = yb.z; y[3] = yb.w;
 #pragma unroll
