@@ -148,6 +148,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(ms, moves, device):
+    """Replicas: the job's time is the slowest rank's timed region, its work the
+    sum of every rank's moves (a no-op for one process)."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    mv = torch.tensor([float(moves)], dtype=torch.float64, device=device)
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(mv, op=tdist.ReduceOp.SUM)
+    return float(t.item()), float(mv.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -236,14 +249,7 @@ def run_gpu(args):
                          "cand_per_iter": round((a["walks"]["cand"] - b["walks"]["cand"]) / max(it, 1), 2),
                          "best_score": a["score"]})
 
-    # max over ranks of the timed region; sum of the work
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    mv = torch.tensor([float(moves)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(mv, op=tdist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    total_moves = float(mv.item())
+    ms_max, total_moves = reduce_over_ranks(ms, moves, "cuda")
     value = total_moves / (ms_max / 1e3)
 
     # roofline of the dominant kernel (the local search), live from this run
