@@ -265,8 +265,9 @@ def run_gpu(args):
                 "frac": round(achieved / smem_peak, 4) if achieved else None,
                 "traffic": (round(LS_DRAM_BYTES_PER_MOVE * wdelta["moves"] / launches_ls)
                             if LS_DRAM_BYTES_PER_MOVE else None),
-                "traffic_note": "DRAM bytes per launch, scaled by moves from an ncu capture of a launch "
-                                "with benchmark-length walks (profiles/)",
+                "traffic_note": "DRAM bytes per launch, scaled by moves from one ncu capture of a "
+                                "launch with benchmark-length walks (%.1f B per move)"
+                                % (LS_DRAM_BYTES_PER_MOVE or 0.0),
                 "kernel": "local_search_kernel",
                 "peak_source": "derived: %d SMs x 128 B/clk x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
                                % (sm_count, sm_max),
