@@ -97,7 +97,10 @@ typedef struct {
  * l and the bound, and uploads them to the current device.  *out is written
  * only on success.  The handle is not thread-safe: one host thread at a time. */
 int  plse_create(int n, const int8_t *grid, plse_handle *out);
-/* Frees every host and device resource of `h`; NULL is accepted. */
+/* Frees every host and device resource of `h`; NULL is accepted.  Device memory
+ * goes back to the library's stream-ordered pool after the last work enqueued
+ * for `h` (on any stream) has run; the call waits only for a run's generations
+ * in flight, never for the whole device. */
 void plse_destroy(plse_handle h);
 /* Static description of an error code; never NULL. */
 const char *plse_strerror(int code);
@@ -217,7 +220,9 @@ int  plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count, int max_
  *     a running one stops enqueueing generations and completes with
  *     PLSE_ECANCELLED and its best so far once its generations in flight end.
  *   pending: requests waiting for admission and results not yet polled.
- *   destroy: cancels what is waiting or running, joins the threads, frees all. */
+ *   destroy: cancels what is waiting or running, joins the threads, frees all.
+ * Every call except destroy may come from any host thread at any time; destroy
+ * must not overlap another call on the same server. */
 typedef struct plse_server_s *plse_server;
 int  plse_server_create(int max_inflight, int max_queue, plse_server *out);
 int  plse_server_submit(plse_server s, int n, const int8_t *grid, const plse_job *job,
