@@ -173,10 +173,10 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # DRAM bytes per tabu move of local_search_kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a launch with walks as long
-# as the benchmark's (bench.py --ls-case 0.3 --pop 1824 --ls-iters 34300
-# --steps 1: 253.8 MB for 2.212e7 moves); scaled to a benchmark launch by its
-# moves.  None whenever the kernel has changed since the capture.
-LS_DRAM_BYTES_PER_MOVE = (124304896 + 129449472) / 22.1241e6   # 11.47 B per move
+# as the benchmark's (bench.py --ls-case 0.3 --pop 2432 --ls-iters 34300
+# --steps 1); scaled to a benchmark launch by its moves.  None whenever the
+# kernel has changed since the capture.
+LS_DRAM_BYTES_PER_MOVE = None
 
 
 def walk_bytes(w):

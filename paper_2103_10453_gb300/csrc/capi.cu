@@ -241,6 +241,8 @@ int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
     if (rc) return rc;
     rc = grow(h, ws.XR, ws.XR_cap, (size_t)slots * 2 * h->di.n * h->di.n1p, false, st);   // idem
     if (rc) return rc;
+    rc = grow(h, ws.HP, ws.HP_cap, (size_t)slots * hp_words(h->di), false, st);          // idem
+    if (rc) return rc;
     rc = grow(h, ws.slot_clock, ws.clock_cap, (size_t)slots, true, st);
     if (rc) return rc;
     return grow(h, ws.counters, ws.counters_cap, 8, true, st);
@@ -283,6 +285,7 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.TC = h->ws.TC;
     a.LIST = h->ws.LIST;
     a.XR = h->ws.XR;
+    a.HP = h->ws.HP;
     a.slot_clock = h->ws.slot_clock;
     a.work_counter = h->ws.counters;
     a.error_flag = h->ws.counters + 1;
@@ -367,6 +370,7 @@ void plse_destroy(plse_handle h)
     dev_free(ws.TC, st);
     dev_free(ws.LIST, st);
     dev_free(ws.XR, st);
+    dev_free(ws.HP, st);
     dev_free(ws.slot_clock, st);
     dev_free(ws.counters, st);
     if (h->done_ev) cudaEventDestroy(h->done_ev);

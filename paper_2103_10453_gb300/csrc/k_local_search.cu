@@ -40,7 +40,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t kRebaseAt = 49152;   // relative clock rebased before it reaches this
 constexpr uint32_t kRebaseBy = 32768;
 constexpr unsigned long long kNoKey = ~0ull;
-constexpr int kPlanes = 8;              // plane slots per 32-colour word (7 used)
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies,
 // a word permutation and a key xor; Weyl key schedule.
@@ -66,12 +65,18 @@ __device__ __forceinline__ int tenure_div(const LSArgs &a, int x)
 }
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-__host__ __device__ inline int colour_words(int n) { return n < 32 ? 1 : n < 64 ? 2 : n < 96 ? 3 : 4; }
 
-// threads per block of the local search: 12 one-warp walks when one block is
-// resident per SM (n >= 64, register-limited at 168), 8 when two are (n < 64)
+// threads per block of the local search: one block per SM at n >= 64 with 16
+// one-warp walks (n < 96) or 12 (n >= 96, whose kernel needs more registers),
+// two blocks of 8 walks per SM below
 template <int NWC>
-constexpr int kMaxThreads = NWC >= 3 ? 384 : 256;
+constexpr int kMaxThreads = NWC == 3 ? 512 : NWC == 4 ? 384 : 256;
+
+// colour counts per (line, 32-colour word) are bit planes: planes 0, 1 and the OR
+// of planes 2..6 (a count >= 4) in shared memory, planes 2..6 in global memory,
+// where they are touched only when a count crosses a multiple of 4
+constexpr int kLo = 4;    // shared words: plane 0, plane 1, high OR, pad
+constexpr int kHi = 8;    // global words: planes 2..6, pad
 
 __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
 {
@@ -80,8 +85,8 @@ __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
     p.inst = align16(align16(2 * (size_t)I.nv) + 32 * (size_t)I.n + 2 * (size_t)I.n);
     size_t o = 0;
     p.off_S = o;      o = align16(o + (size_t)I.nv);
-    p.off_RP = o;     o += 32 * (size_t)I.n * cw;
-    p.off_KP = o;     o += 32 * (size_t)I.n * cw;
+    p.off_RP = o;     o += 4 * kLo * (size_t)I.n * cw;
+    p.off_KP = o;     o += 4 * kLo * (size_t)I.n * cw;
     p.off_cmask = o;  o += 4 * (size_t)I.nw;
     p.off_lmask = o;  o += 4 * (size_t)I.nw;
     p.off_red = align16(o);
@@ -94,7 +99,8 @@ __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
 // One walk's shared-memory slot.
 struct Slot {
     uint8_t *S;                 // current colouring [nv]
-    uint32_t *RP, *KP;          // colour-count bit planes [n][cw][8] per row / per column
+    uint32_t *RP, *KP;          // colour-count planes 0, 1 and high OR [n][cw][kLo] per row / column
+    uint32_t *RH, *KH;          // colour-count planes 2..6 [n][cw][kHi] per row / column, global
     uint32_t *cmask;            // candidate bitmask [nw]
     uint32_t *lmask;            // vertices present in the candidate list [nw]
     uint16_t *list;             // candidate list (may hold stale entries) [nv], global memory
@@ -144,6 +150,7 @@ __device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I)
     c.s.cmask = reinterpret_cast<uint32_t *>(sb + p.off_cmask);
     c.s.lmask = reinterpret_cast<uint32_t *>(sb + p.off_lmask);
     c.s.list = nullptr;         // set once the walk slot is known
+    c.s.RH = c.s.KH = nullptr;
     c.s.xr = nullptr;
     c.s.tc = nullptr;           // set once the walk slot is known
     c.s.red = reinterpret_cast<unsigned long long *>(sb + p.off_red);
@@ -212,112 +219,113 @@ __device__ __forceinline__ void gcopy(uint8_t *dst, const uint8_t *src, int n, c
 // ---- colour-count planes ----------------------------------------------------
 __device__ __forceinline__ const uint32_t *line_planes(const uint32_t *P, int cw, int line)
 {
-    return P + (size_t)line * cw * kPlanes;
+    return P + (size_t)line * cw * kLo;
 }
 
-// +1 / -1 on count[line][k] (one thread per line at a time).  Returns the change
-// in the number of counts >= 4 (planes 2..6), which selects the evaluation path.
-__device__ __forceinline__ int count_step(uint32_t *P, int cw, int line, int k, bool inc)
+__device__ __forceinline__ uint4 *lo_word(const Ctx &c, int side, int line, int k)
 {
-    uint4 *w = reinterpret_cast<uint4 *>(P + ((size_t)line * cw + (k >> 5)) * kPlanes);
-    uint4 a = w[0], b = w[1];
-    uint32_t x[7] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
-    const uint32_t bit = 1u << (k & 31);
-    const int old_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
-    uint32_t carry = bit;
-#pragma unroll
-    for (int p = 0; p < 7; ++p) {
-        const uint32_t t = inc ? (x[p] & carry) : (~x[p] & carry);
-        x[p] ^= carry;
-        carry = t;
-    }
-    w[0] = make_uint4(x[0], x[1], x[2], x[3]);
-    w[1] = make_uint4(x[4], x[5], x[6], b.w);
-    const int new_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
-    return new_hi - old_hi;
+    return reinterpret_cast<uint4 *>(side ? c.s.KP : c.s.RP) + (size_t)line * c.cw + (k >> 5);
 }
 
-// count of colour k from the seven plane words of its 32-colour word
-__device__ __forceinline__ int count_in(const uint32_t (&x)[7], int k)
+__device__ __forceinline__ uint32_t *hi_words(const Ctx &c, int side, int line, int k)
+{
+    return (side ? c.s.KH : c.s.RH) + ((size_t)line * c.cw + (k >> 5)) * kHi;
+}
+
+// +1 / -1 on count[side][line][k] (one thread per line at a time).  Returns the
+// change in the number of counts >= 4, which selects the evaluation path, and
+// the updated shared word in *lo_out (may be null).
+__device__ __forceinline__ int count_step(const Ctx &c, int side, int line, int k, bool inc, uint4 *lo_out = nullptr)
+{
+    uint4 *w = lo_word(c, side, line, k);
+    uint4 a = *w;
+    const uint32_t bit = 1u << (k & 31);
+    const int old_hi = (a.z & bit) ? 1 : 0;
+    uint32_t carry = bit, t;
+    t = inc ? (a.x & carry) : (~a.x & carry);
+    a.x ^= carry;
+    carry = t;
+    t = inc ? (a.y & carry) : (~a.y & carry);
+    a.y ^= carry;
+    carry = t;
+    if (carry) {                                   // crosses a multiple of 4: planes 2..6
+        uint32_t *g = hi_words(c, side, line, k);
+        const uint4 g0 = *reinterpret_cast<const uint4 *>(g);
+        uint32_t x[5] = {g0.x, g0.y, g0.z, g0.w, g[4]};
+#pragma unroll
+        for (int p = 0; p < 5; ++p) {
+            t = inc ? (x[p] & carry) : (~x[p] & carry);
+            x[p] ^= carry;
+            carry = t;
+        }
+        *reinterpret_cast<uint4 *>(g) = make_uint4(x[0], x[1], x[2], x[3]);
+        g[4] = x[4];
+        a.z = ((x[0] | x[1] | x[2] | x[3] | x[4]) & bit) ? (a.z | bit) : (a.z & ~bit);
+    }
+    *w = a;
+    if (lo_out) *lo_out = a;
+    return ((a.z & bit) ? 1 : 0) - old_hi;
+}
+
+// count from a shared word: exact below 4, reported as 4 + (count mod 4) from 4 on,
+// which decides every "count > t" test with t <= 3 like the exact count
+__device__ __forceinline__ int count_low(const uint4 &a, int k)
 {
     const uint32_t b = k & 31;
-    int c = 0;
-#pragma unroll
-    for (int p = 0; p < 7; ++p) c |= (int)((x[p] >> b) & 1u) << p;
-    return c;
+    return (int)(((a.x >> b) & 1u) | (((a.y >> b) & 1u) << 1) | (((a.z >> b) & 1u) << 2));
 }
 
-// count_step that also returns the updated plane words in x
-__device__ __forceinline__ int count_step_words(uint32_t *P, int cw, int line, int k, bool inc, uint32_t (&xo)[7])
+__device__ __forceinline__ int count_of_fast(const Ctx &c, int side, int line, int k)
 {
-    uint4 *w = reinterpret_cast<uint4 *>(P + ((size_t)line * cw + (k >> 5)) * kPlanes);
-    uint4 a = w[0], b = w[1];
-    uint32_t x[7] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
-    const uint32_t bit = 1u << (k & 31);
-    const int old_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
-    uint32_t carry = bit;
-#pragma unroll
-    for (int p = 0; p < 7; ++p) {
-        const uint32_t t = inc ? (x[p] & carry) : (~x[p] & carry);
-        x[p] ^= carry;
-        carry = t;
-    }
-    w[0] = make_uint4(x[0], x[1], x[2], x[3]);
-    w[1] = make_uint4(x[4], x[5], x[6], b.w);
-#pragma unroll
-    for (int p = 0; p < 7; ++p) xo[p] = x[p];
-    const int new_hi = ((x[2] | x[3] | x[4] | x[5] | x[6]) & bit) ? 1 : 0;
-    return new_hi - old_hi;
+    return count_low(*lo_word(c, side, line, k), k);
 }
 
-__device__ __forceinline__ int count_of(const uint32_t *P, int cw, int line, int k)
+// exact count (planes 2..6 read from global memory only when the count is >= 4)
+__device__ __forceinline__ int count_of(const Ctx &c, int side, int line, int k)
 {
-    const uint32_t *w = P + ((size_t)line * cw + (k >> 5)) * kPlanes;
-    const uint4 a = *reinterpret_cast<const uint4 *>(w);
-    const uint4 b4 = *reinterpret_cast<const uint4 *>(w + 4);
+    const uint4 a = *lo_word(c, side, line, k);
     const uint32_t b = k & 31;
-    const uint32_t x = ((a.x >> b) & 1u) | (((a.y >> b) & 1u) << 1) | (((a.z >> b) & 1u) << 2) |
-                       (((a.w >> b) & 1u) << 3) | (((b4.x >> b) & 1u) << 4) | (((b4.y >> b) & 1u) << 5) |
-                       (((b4.z >> b) & 1u) << 6);
-    return (int)x;
+    int x = (int)(((a.x >> b) & 1u) | (((a.y >> b) & 1u) << 1));
+    if ((a.z >> b) & 1u) {
+        const uint32_t *g = hi_words(c, side, line, k);
+#pragma unroll
+        for (int p = 0; p < 5; ++p) x |= (int)((g[p] >> b) & 1u) << (p + 2);
+    }
+    return x;
 }
 
 __device__ __forceinline__ int gamma_of(const DevInst &I, const Ctx &c, int v, int k)
 {
     const uint16_t rc = c.rc[v];
-    return count_of(c.s.RP, c.cw, rc >> 8, k) + count_of(c.s.KP, c.cw, rc & 255, k) - 2;
+    return count_of(c, 0, rc >> 8, k) + count_of(c, 1, rc & 255, k) - 2;
 }
 
 template <int NW>
 __device__ __forceinline__ void build_planes(const DevInst &I, const Ctx &c)
 {
-    uint32_t *P = c.s.RP;   // RP and KP are contiguous
-    const int words = 2 * I.n * c.cw * kPlanes;
-    for (int q = c.gt; q < words; q += 32 * NW) P[q] = 0u;
+    const int lo_words = 2 * I.n * c.cw * kLo, hi_words_n = 2 * I.n * c.cw * kHi;
+    for (int q = c.gt; q < lo_words; q += 32 * NW) c.s.RP[q] = 0u;   // RP and KP are contiguous
+    for (int q = c.gt; q < hi_words_n; q += 32 * NW) c.s.RH[q] = 0u;  // RH and KH are contiguous
     gsync<NW>(c);
     for (int l = c.gt; l < 2 * I.n; l += 32 * NW) {
         const bool col = l >= I.n;
         const int line = col ? l - I.n : l;
         const int32_t *ptr = col ? I.col_ptr : I.row_ptr;
         const uint16_t *lst = col ? I.col_v : I.row_v;
-        uint32_t *T = col ? c.s.KP : c.s.RP;
         uint16_t *X = c.s.xr + (size_t)l * I.n1p;
         for (int k = 0; k < I.n1p; ++k) X[k] = 0;
         for (int q = __ldg(&ptr[line]); q < __ldg(&ptr[line + 1]); ++q) {
             const int u = __ldg(&lst[q]);
             const int k = c.s.S[u];
             if (k) {
-                count_step(T, c.cw, line, k, true);
+                count_step(c, col ? 1 : 0, line, k, true);
                 X[k] ^= (uint16_t)u;
             }
         }
     }
     gsync<NW>(c);
     int hi = 0;
-    for (int t = c.gt; t < 2 * I.n * c.cw; t += 32 * NW) {
-        const uint32_t *w = c.s.RP + (size_t)t * kPlanes;
-        hi += __popc(w[2] | w[3] | w[4] | w[5] | w[6]);
-    }
+    for (int t = c.gt; t < 2 * I.n * c.cw; t += 32 * NW) hi += __popc(c.s.RP[(size_t)t * kLo + 2]);
     hi = gsum<NW>(hi, c);
     if (c.gt == 0) c.s.scal[2] = hi;
     gsync<NW>(c);
@@ -330,7 +338,10 @@ __device__ __forceinline__ int conflict_edges(const DevInst &I, const Ctx &c)
 {
     long long s = 0;
     for (int t = c.gt; t < 2 * I.n * c.cw; t += 32 * NW) {
-        const uint32_t *w = c.s.RP + (size_t)t * kPlanes;
+        const uint32_t *lo = c.s.RP + (size_t)t * kLo, *g = c.s.RH + (size_t)t * kHi;
+        const bool high = lo[2] != 0u;
+        const uint32_t w[7] = {lo[0], lo[1], high ? g[0] : 0u, high ? g[1] : 0u, high ? g[2] : 0u,
+                               high ? g[3] : 0u, high ? g[4] : 0u};
         long long sq = 0, lin = 0;
 #pragma unroll
         for (int p = 0; p < 7; ++p) {
@@ -643,8 +654,8 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
     uint32_t s0[NWC], s1[NWC], s2[NWC];
 #pragma unroll
     for (int q = 0; q < NWC; ++q) {
-        const uint2 ra = *reinterpret_cast<const uint2 *>(RPr + q * kPlanes);
-        const uint2 ka = *reinterpret_cast<const uint2 *>(KPc + q * kPlanes);
+        const uint2 ra = *reinterpret_cast<const uint2 *>(RPr + q * kLo);
+        const uint2 ka = *reinterpret_cast<const uint2 *>(KPc + q * kLo);
         const uint32_t x0 = ra.x ^ ka.x, cy = ra.x & ka.x, x1 = ra.y ^ ka.y;
         s0[q] = x0;
         s1[q] = x1 ^ cy;
@@ -706,12 +717,20 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
     uint32_t s[NWC][8];
 #pragma unroll
     for (int q = 0; q < NWC; ++q) {
-        const uint4 r0 = *reinterpret_cast<const uint4 *>(RPr + q * kPlanes);
-        const uint4 r1 = *reinterpret_cast<const uint4 *>(RPr + q * kPlanes + 4);
-        const uint4 k0 = *reinterpret_cast<const uint4 *>(KPc + q * kPlanes);
-        const uint4 k1 = *reinterpret_cast<const uint4 *>(KPc + q * kPlanes + 4);
-        const uint32_t a[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
-        const uint32_t b[7] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z};
+        const uint4 r0 = *reinterpret_cast<const uint4 *>(RPr + q * kLo);
+        const uint4 k0 = *reinterpret_cast<const uint4 *>(KPc + q * kLo);
+        uint32_t a[7] = {r0.x, r0.y, 0u, 0u, 0u, 0u, 0u};
+        uint32_t b[7] = {k0.x, k0.y, 0u, 0u, 0u, 0u, 0u};
+        if (r0.z) {
+            const uint32_t *g = c.s.RH + ((size_t)r * NWC + q) * kHi;
+#pragma unroll
+            for (int p = 0; p < 5; ++p) a[p + 2] = g[p];
+        }
+        if (k0.z) {
+            const uint32_t *g = c.s.KH + ((size_t)cc * NWC + q) * kHi;
+#pragma unroll
+            for (int p = 0; p < 5; ++p) b[p + 2] = g[p];
+        }
         uint32_t carry = 0u;
 #pragma unroll
         for (int p = 0; p < 7; ++p) {
@@ -721,7 +740,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
         }
         s[q][7] = carry;
     }
-    const int gi = i ? count_of(c.s.RP, NWC, r, i) + count_of(c.s.KP, NWC, cc, i) - 2 : 0;
+    const int gi = i ? count_of(c, 0, r, i) + count_of(c, 1, cc, i) - 2 : 0;
     const int base2 = i ? -mult * gi : base_unc;
     const int d2zero = 2 - mult * gi;
     const uint4 ar = c.allow[r], ac = c.allow[I.n + cc];
@@ -754,7 +773,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
                 }
             } else if (cs < 128u && test_bit<NWC>(m, cs)) {
                 clear_bit<NWC>(m, cs);
-                const int d2 = base2 + mult * (count_of(c.s.RP, NWC, r, (int)cs) + count_of(c.s.KP, NWC, cc, (int)cs));
+                const int d2 = base2 + mult * (count_of(c, 0, r, (int)cs) + count_of(c, 1, cc, (int)cs));
                 if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
             }
         }
@@ -776,7 +795,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
             while (bits) {
                 const uint32_t j = q * 32 + __ffs(bits) - 1;
                 bits &= bits - 1;
-                const int d2 = base2 + mult * (count_of(c.s.RP, NWC, r, (int)j) + count_of(c.s.KP, NWC, cc, (int)j));
+                const int d2 = base2 + mult * (count_of(c, 0, r, (int)j) + count_of(c, 1, cc, (int)j));
                 const bool tabu = (j == c0) ? (e0 >= trel) : (j == c1) ? (e1 >= trel) : (Gv[j] >= tabs);
                 if (!tabu || d2 < A) best = min(best, d2 * kKeyScale + (int)j);
             }
@@ -993,18 +1012,18 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             const int xold = (c.lane < 4 && xk) ? (int)c.s.xr[xidx] : 0;
             int cnt_i = 0, cnt_j = 0;
             if (c.lane < 4) {
-                uint32_t *P = (c.lane & 1) ? c.s.KP : c.s.RP;
-                const int line = (c.lane & 1) ? cc : r;
+                const int side = c.lane & 1;
+                const int line = side ? cc : r;
                 int dh = 0;
-                uint32_t w[7];
+                uint4 w;
                 if (c.lane < 2) {
-                    if (i) dh += count_step_words(P, c.cw, line, i, false, w);
-                    if (same) dh += count_step_words(P, c.cw, line, j, true, w);
-                    if (i) cnt_i = count_in(w, i);       // counts after the move
-                    if (same) cnt_j = count_in(w, j);
+                    if (i) dh += count_step(c, side, line, i, false, &w);
+                    if (same) dh += count_step(c, side, line, j, true, &w);
+                    if (i) cnt_i = count_low(w, i);       // counts after the move (4 = four or more)
+                    if (same) cnt_j = count_low(w, j);
                 } else if (j && !same) {
-                    dh += count_step_words(P, c.cw, line, j, true, w);
-                    cnt_j = count_in(w, j);
+                    dh += count_step(c, side, line, j, true, &w);
+                    cnt_j = count_low(w, j);
                 }
                 if (dh) atomicAdd(&c.s.scal[2], dh);
                 if (c.lane == 0) c.s.S[v] = (uint8_t)j;
@@ -1031,8 +1050,8 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
                     bad_mate = true;                     // inconsistent table: report, touch nothing
                 } else {
                     const uint16_t urc = c.rc[u];
-                    const int g = cl + (row_mate ? count_of(c.s.KP, c.cw, urc & 255, su)
-                                                 : count_of(c.s.RP, c.cw, urc >> 8, su)) - 2;
+                    const int g = cl + (row_mate ? count_of_fast(c, 1, urc & 255, su)
+                                                 : count_of_fast(c, 0, urc >> 8, su)) - 2;
                     const int nc = g > 0, oc = (c.s.cmask[u >> 5] >> (u & 31)) & 1;
                     if (nc != oc) {
                         atomicXor(&c.s.cmask[u >> 5], 1u << (u & 31));
@@ -1097,7 +1116,7 @@ __device__ __forceinline__ void repair(const DevInst &I, const Ctx &c)
             const int k = c.s.S[v];
             const uint16_t rc = c.rc[v];
             c.s.S[v] = 0;
-            c.s.scal[2] += count_step(c.s.RP, c.cw, rc >> 8, k, false) + count_step(c.s.KP, c.cw, rc & 255, k, false);
+            c.s.scal[2] += count_step(c, 0, rc >> 8, k, false) + count_step(c, 1, rc & 255, k, false);
         }
         gsync<NW>(c);
     }
@@ -1220,13 +1239,13 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
                         const int u = ulist[k];
                         const uint16_t rcu = c.rc[u];
                         c.s.S[u] = 0;
-                        c.s.scal[2] += count_step(c.s.RP, c.cw, rcu >> 8, j, false) +
-                                       count_step(c.s.KP, c.cw, rcu & 255, j, false);
+                        c.s.scal[2] += count_step(c, 0, rcu >> 8, j, false) +
+                                       count_step(c, 1, rcu & 255, j, false);
                         atomicOr(&c.s.cmask[u >> 5], 1u << (u & 31));
                         tabu_insert(I, c, G, ck, u, j, trel + (uint32_t)T);
                     }
                     c.s.S[v] = (uint8_t)j;
-                    c.s.scal[2] += count_step(c.s.RP, c.cw, r, j, true) + count_step(c.s.KP, c.cw, cc, j, true);
+                    c.s.scal[2] += count_step(c, 0, r, j, true) + count_step(c, 1, cc, j, true);
                     atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
                 }
                 __syncwarp();
@@ -1279,6 +1298,8 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
     c.s.tc = a.TC + (size_t)slot * I.nv;
     c.s.list = a.LIST + (size_t)slot * I.nv;
     c.s.xr = a.XR + (size_t)slot * 2 * I.n * I.n1p;
+    c.s.RH = a.HP + (size_t)slot * 2 * I.n * c.cw * kHi;
+    c.s.KH = c.s.RH + (size_t)I.n * c.cw * kHi;
 
     for (;;) {
         if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);
@@ -1417,10 +1438,11 @@ LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps, i
     int max_smem = 0, sms = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    // one block per SM holding as many walk slots as fit (at most 384 threads at
-    // n >= 64, where one block is resident per SM; 256 below, with two blocks)
+    // one block per SM holding as many walk slots as fit (at most kMaxThreads
+    // threads: 512 for 64 <= n < 96, 384 from 96, 256 below 64 with two blocks)
     long long walks = ((long long)max_smem - (long long)p.inst) / (long long)p.slot;
-    const int max_threads = L.colour_words >= 3 ? kMaxThreads<3> : kMaxThreads<1>;
+    const int max_threads = L.colour_words == 1 ? kMaxThreads<1> : L.colour_words == 2 ? kMaxThreads<2>
+                          : L.colour_words == 3 ? kMaxThreads<3> : kMaxThreads<4>;
     walks = std::min<long long>(walks, std::max(1, max_threads / (32 * L.warps)));
     if (max_walks > 0) walks = std::min<long long>(walks, max_walks);
     if (walks < 1) {

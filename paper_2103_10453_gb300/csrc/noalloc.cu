@@ -83,10 +83,11 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
 
     // walk slots that fit: each needs an evicted-tabu table (4 * |V| * n1p bytes),
     // a tabu cache (8 * |V| bytes), a candidate list (2 * |V| bytes), a member-id
-    // XOR table (4 * n * n1p bytes) and a clock word
+    // XOR table (4 * n * n1p bytes), the high colour-count planes and a clock word
     const size_t xr_bytes = 4 * (size_t)h->di.n * h->di.n1p;
-    const size_t table_bytes = 4 * (size_t)h->di.nv * h->di.n1p + 10 * (size_t)h->di.nv + xr_bytes;
-    const size_t max_slots = (kNoAllocScratchBytes - kCounterBytes - 1280) / (table_bytes + 4);   // 1280: alignment
+    const size_t hp_bytes = 4 * hp_words(h->di);
+    const size_t table_bytes = 4 * (size_t)h->di.nv * h->di.n1p + 10 * (size_t)h->di.nv + xr_bytes + hp_bytes;
+    const size_t max_slots = (kNoAllocScratchBytes - kCounterBytes - 1536) / (table_bytes + 4);   // 1536: alignment
     if (max_slots < 1)
         return fail(h, PLSE_ENOTSUP,
                     "plse_local_search_noalloc: one walk slot needs %zu bytes of scratch, more than the %zu "
@@ -103,7 +104,8 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     }
     const size_t slots = (size_t)L.slots();
     // layout: [counters][slot clocks][evicted-tabu tables][tabu caches][lists][XOR
-    // tables]; the first three must start at zero, the rest is rebuilt by every phase
+    // tables][high planes]; the first three must start at zero, the rest is rebuilt
+    // by every phase
     int *counters = reinterpret_cast<int *>(scratch);
     uint32_t *clocks = reinterpret_cast<uint32_t *>(scratch + kCounterBytes);
     const size_t tables_off = (kCounterBytes + 4 * slots + 255) & ~size_t(255);
@@ -114,7 +116,9 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     uint16_t *lists = reinterpret_cast<uint16_t *>(scratch + list_off);
     const size_t xr_off = (list_off + slots * 2 * (size_t)h->di.nv + 255) & ~size_t(255);
     uint16_t *xrs = reinterpret_cast<uint16_t *>(scratch + xr_off);
-    const size_t used = xr_off + slots * xr_bytes;
+    const size_t hp_off = (xr_off + slots * xr_bytes + 255) & ~size_t(255);
+    uint32_t *hps = reinterpret_cast<uint32_t *>(scratch + hp_off);
+    const size_t used = hp_off + slots * hp_bytes;
     if (used > kNoAllocScratchBytes) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: scratch overflow");
     e = cudaMemsetAsync(scratch, 0, tc_off, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "plse_local_search_noalloc: clear scratch");
@@ -147,6 +151,7 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     a.TC = tcache;
     a.LIST = lists;
     a.XR = xrs;
+    a.HP = hps;
     a.slot_clock = clocks;
     a.work_counter = counters;
     a.error_flag = counters + 1;

@@ -22,6 +22,8 @@ struct Workspace {
     size_t LIST_cap = 0;
     uint16_t *XR = nullptr;         // member-id XOR tables, one per walk slot
     size_t XR_cap = 0;
+    uint32_t *HP = nullptr;         // colour-count planes 2..6, one set per walk slot
+    size_t HP_cap = 0;
     uint32_t *slot_clock = nullptr; // per-slot clock
     size_t clock_cap = 0;
     int *counters = nullptr;        // [0] walk counter, [1] error flag, [2..] spare

@@ -58,6 +58,7 @@ struct LSArgs {
     uint2 *TC;                    // [slots][nv] two-entry tabu caches (relative clock)
     uint16_t *LIST;               // [slots][nv] candidate lists
     uint16_t *XR;                 // [slots][2n][n1p] member-id XOR per line and colour
+    uint32_t *HP;                 // [slots][2n][cw][8] colour-count planes 2..6
     uint32_t *slot_clock;         // [slots] next free clock value of each slot
     int *work_counter;            // dynamic walk scheduler, zeroed before launch
     int *error_flag;              // nonzero after a failed device bound check
@@ -88,5 +89,12 @@ cudaError_t launch_local_search(const DevInst &I, const LSArgs &a, const LSLaunc
                                 cudaStream_t st);
 // warps = 0: automatic.  max_walks caps the walks per block (0 = no cap).
 LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps, int max_walks = 0);
+
+// 32-colour words of a colour mask over colours 0..n
+__host__ __device__ inline int colour_words(int n) { return n < 32 ? 1 : n < 64 ? 2 : n < 96 ? 3 : 4; }
+
+// u32 words per walk slot of the colour-count planes 2..6 kept in global memory
+// ([2n lines][colour words][8])
+inline size_t hp_words(const DevInst &I) { return 2 * (size_t)I.n * colour_words(I.n) * 8; }
 
 }  // namespace plse
