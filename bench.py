@@ -174,9 +174,9 @@ def measured_peaks():
 # DRAM bytes per tabu move of local_search_kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a launch with walks as long
 # as the benchmark's (bench.py --ls-case 0.3 --pop 2432 --ls-iters 34300
-# --steps 1); scaled to a benchmark launch by its moves.  None whenever the
-# kernel has changed since the capture.
-LS_DRAM_BYTES_PER_MOVE = None
+# --steps 1: 467.8 MB for 2.972e7 moves); scaled to a benchmark launch by its
+# moves.  None whenever the kernel has changed since the capture.
+LS_DRAM_BYTES_PER_MOVE = (216190464 + 251600896) / 29.7232e6   # 15.74 B per move
 
 
 def walk_bytes(w):
@@ -265,9 +265,9 @@ def run_gpu(args):
                 "frac": round(achieved / smem_peak, 4) if achieved else None,
                 "traffic": (round(LS_DRAM_BYTES_PER_MOVE * wdelta["moves"] / launches_ls)
                             if LS_DRAM_BYTES_PER_MOVE else None),
-                "traffic_note": "DRAM bytes per launch, scaled by moves from one ncu capture of a "
-                                "launch with benchmark-length walks (%.1f B per move)"
-                                % (LS_DRAM_BYTES_PER_MOVE or 0.0),
+                "traffic_note": ("DRAM bytes per launch, scaled by moves from one ncu capture of a "
+                                 "launch with benchmark-length walks (%.1f B per move)" % LS_DRAM_BYTES_PER_MOVE
+                                 if LS_DRAM_BYTES_PER_MOVE else "no capture of the current kernel"),
                 "kernel": "local_search_kernel",
                 "peak_source": "derived: %d SMs x 128 B/clk x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
                                % (sm_count, sm_max),
