@@ -500,24 +500,6 @@ __device__ __forceinline__ bool test_bit(const uint32_t (&m)[NWC], uint32_t k)
     return (w >> (k & 31)) & 1u;
 }
 
-// s_k from the summed planes held in registers
-template <int NWC>
-__device__ __forceinline__ int plane_value(const uint32_t (&s)[NWC][8], uint32_t k)
-{
-    uint32_t sel[NWC];
-    word_masks<NWC>(k, sel);
-    const uint32_t b = k & 31;
-    int x = 0;
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        uint32_t w = 0;
-#pragma unroll
-        for (int q = 0; q < NWC; ++q) w |= s[q][p] & sel[q];
-        x |= (int)((w >> b) & 1u) << p;
-    }
-    return x;
-}
-
 // min over colours j in m of s_j (lowest j on ties) by most-significant-plane-
 // first elimination; returns -1 if m is empty
 template <int NWC>

@@ -76,8 +76,8 @@ struct LSLaunch {
 
 // Shared-memory plan of one block (bytes): instance part, then `walks` slots.
 struct SmemPlan {
-    size_t inst;       // vertex coordinates and allowed-colour masks
-    size_t slot;       // one walk: colouring, count planes, candidate set, tabu cache, scalars
+    size_t inst;       // vertex coordinates, allowed-colour masks and line lengths
+    size_t slot;       // one walk: colouring, count words (planes 0-1, high OR), candidate masks, scalars
     size_t off_S, off_RP, off_KP, off_cmask, off_lmask, off_red;   // within a slot
     size_t total(int walks) const { return inst + slot * (size_t)walks; }
 };
