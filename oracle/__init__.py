@@ -84,6 +84,10 @@ def _load():
         lib.or_tabu_walk.restype = C.c_int64
         lib.or_tabu_walk.argtypes = [C.c_void_p, P(Params), u8p, C.c_int32, C.c_int32,
                                      C.c_int32, C.c_int64, C.c_uint64, C.c_int32, P(Stats)]
+        lib.or_tabu_walk_traced.restype = C.c_int64
+        lib.or_tabu_walk_traced.argtypes = [C.c_void_p, P(Params), u8p, C.c_int32, C.c_int32,
+                                            C.c_int32, C.c_int64, C.c_uint64, C.c_int32,
+                                            P(Stats), i32p]
         lib.or_repair.restype = C.c_int32
         lib.or_repair.argtypes = [C.c_void_p, u8p]
         lib.or_distances.argtypes = [C.c_void_p, u8p, C.c_int32, u8p, C.c_int32, i32p]
@@ -195,6 +199,22 @@ class Instance:
         if r < 0:
             raise OracleError("walk self-check failed or start colouring illegal")
         return S, int(r), st.as_dict()
+
+    def tabu_walk_traced(self, S, ind, gen, phase, iters, seed, params=None):
+        """Alg. 3 as ``tabu_walk``, also returning the move chosen at each
+        iteration executed: an int32 array [iterations, 3] of (v, colour before,
+        colour after), (-1, -1, -1) where no move was admissible."""
+        params = params or default_params()
+        S = np.array(S, dtype=np.uint8, copy=True, order="C")
+        st = Stats()
+        trace = np.full((max(int(iters), 1), 3), -2, dtype=np.int32)
+        r = self.lib.or_tabu_walk_traced(self.h, C.byref(params), _ptr(S, C.c_uint8), ind, gen,
+                                         phase, int(iters), seed, 0, C.byref(st),
+                                         _ptr(trace, C.c_int32))
+        if r < 0:
+            raise OracleError("start colouring illegal")
+        stats = st.as_dict()
+        return S, int(r), stats, trace[:stats["iterations"]].copy()
 
     def repair(self, S):
         S = np.array(S, dtype=np.uint8, copy=True, order="C")

@@ -308,7 +308,7 @@ static int key_less(int64_t d2, int rot, int j, const MoveKey *b)
 
 static int64_t plits_walk(const Inst *I, const or_params *prm, uint8_t *S, int32_t ind,
                           int32_t gen, int32_t phase, int64_t iters, uint64_t seed,
-                          int32_t debug, or_stats *st)
+                          int32_t debug, or_stats *st, int32_t *trace)
 {
     const int n1 = I->n + 1, nv = I->nv;
     const int64_t phi2 = (phase == 1) ? prm->phase1_phi2
@@ -336,6 +336,7 @@ static int64_t plits_walk(const Inst *I, const or_params *prm, uint8_t *S, int32
         }
         if (ncand == 0) break;            /* f = c = 0: nothing left to improve */
         if (st) { st->iterations++; st->cand += ncand; }
+        if (trace) trace[3 * (t - 1)] = trace[3 * (t - 1) + 1] = trace[3 * (t - 1) + 2] = -1;
 
         uint32_t u[4];
         draw4(seed, (uint32_t)t, (uint32_t)ind, (uint32_t)gen, PURPOSE_TABU, (uint32_t)phase, u);
@@ -372,6 +373,7 @@ static int64_t plits_walk(const Inst *I, const or_params *prm, uint8_t *S, int32
 
         /* apply S <- S (+) <v, V_i, V_j> and update gamma incrementally */
         const int v = bestm.v, j = bestm.j, i = S[v];
+        if (trace) { trace[3 * (t - 1)] = v; trace[3 * (t - 1) + 1] = i; trace[3 * (t - 1) + 2] = j; }
         if (st) { st->moves++; st->deg += I->adj_ptr[v + 1] - I->adj_ptr[v]; }
         f += (j == 0) - (i == 0);
         c += (j ? gamma[v * n1 + j] : 0) - (i ? gamma[v * n1 + i] : 0);
@@ -408,7 +410,7 @@ out:
 
 static int64_t partialcol_walk(const Inst *I, const or_params *prm, uint8_t *S, int32_t ind,
                                int32_t gen, int64_t iters, uint64_t seed, int32_t debug,
-                               or_stats *st)
+                               or_stats *st, int32_t *trace)
 {
     const int n1 = I->n + 1, nv = I->nv;
     int32_t *gamma = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv * n1 + 4);
@@ -427,6 +429,7 @@ static int64_t partialcol_walk(const Inst *I, const or_params *prm, uint8_t *S, 
     for (int64_t t = 1; t <= iters; ++t) {
         if (f == 0) break;
         if (st) { st->iterations++; st->cand += f; }
+        if (trace) trace[3 * (t - 1)] = trace[3 * (t - 1) + 1] = trace[3 * (t - 1) + 2] = -1;
         uint32_t u[4];
         draw4(seed, (uint32_t)t, (uint32_t)ind, (uint32_t)gen, PURPOSE_TABU, 3u, u);
         const int64_t L = bounded(u[0], (uint32_t)prm->tenure_rand);
@@ -451,6 +454,7 @@ static int64_t partialcol_walk(const Inst *I, const or_params *prm, uint8_t *S, 
         if (!bestm.valid) continue;
 
         const int v = bestm.v, j = bestm.j;
+        if (trace) { trace[3 * (t - 1)] = v; trace[3 * (t - 1) + 1] = 0; trace[3 * (t - 1) + 2] = j; }
         if (st) { st->moves++; st->deg += I->adj_ptr[v + 1] - I->adj_ptr[v]; }
         /* neighbours currently coloured j lose their colour */
         int unc[2 * 128], nunc = 0;
@@ -488,13 +492,20 @@ out:
     return ret;
 }
 
-int64_t or_tabu_walk(const void *h, const or_params *prm, uint8_t *S, int32_t ind, int32_t gen,
-                     int32_t phase, int64_t iters, uint64_t seed, int32_t debug, or_stats *st)
+int64_t or_tabu_walk_traced(const void *h, const or_params *prm, uint8_t *S, int32_t ind,
+                            int32_t gen, int32_t phase, int64_t iters, uint64_t seed,
+                            int32_t debug, or_stats *st, int32_t *trace)
 {
     const Inst *I = (const Inst *)h;
     if (I->nv == 0) return 0;
-    if (phase == 3) return partialcol_walk(I, prm, S, ind, gen, iters, seed, debug, st);
-    return plits_walk(I, prm, S, ind, gen, phase, iters, seed, debug, st);
+    if (phase == 3) return partialcol_walk(I, prm, S, ind, gen, iters, seed, debug, st, trace);
+    return plits_walk(I, prm, S, ind, gen, phase, iters, seed, debug, st, trace);
+}
+
+int64_t or_tabu_walk(const void *h, const or_params *prm, uint8_t *S, int32_t ind, int32_t gen,
+                     int32_t phase, int64_t iters, uint64_t seed, int32_t debug, or_stats *st)
+{
+    return or_tabu_walk_traced(h, prm, S, ind, gen, phase, iters, seed, debug, st, NULL);
 }
 
 /* ------------------------------------------------------------------ */

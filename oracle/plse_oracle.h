@@ -87,6 +87,13 @@ void or_init_population(const void *h, int32_t p, uint64_t seed, uint8_t *P);
 int64_t or_tabu_walk(const void *h, const or_params *prm, uint8_t *S,
                      int32_t ind, int32_t gen, int32_t phase, int64_t iters,
                      uint64_t seed, int32_t debug, or_stats *st);
+/* As or_tabu_walk, also recording the move chosen at every iteration executed:
+ * trace[3*(t-1) .. 3*(t-1)+2] = (v, colour before, colour after), or (-1, -1, -1)
+ * for an iteration without an admissible move.  trace holds 3*iters int32
+ * (entries past the last executed iteration are left untouched). */
+int64_t or_tabu_walk_traced(const void *h, const or_params *prm, uint8_t *S,
+                            int32_t ind, int32_t gen, int32_t phase, int64_t iters,
+                            uint64_t seed, int32_t debug, or_stats *st, int32_t *trace);
 
 /* Greedy conflict removal (Sec. 3.7): returns the number of vertices uncoloured. */
 int32_t or_repair(const void *h, uint8_t *S);
