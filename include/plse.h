@@ -124,7 +124,7 @@ int  plse_get_params(plse_handle h, plse_params *p);
 
 /* Launch knobs that never change results: warps per walk of the local-search
  * kernel (1, 2, 4 or 8; 0 = automatic) and the cap on concurrent walks per block
- * (0 = as many as fit in shared memory).  Used by the autotuner. */
+ * (0 = as many as fit in shared memory). */
 int  plse_set_launch(plse_handle h, int ls_warps, int ls_walks);
 
 /* ---- whole solve (Alg. 2) ---------------------------------------------------
@@ -267,18 +267,21 @@ int  plse_local_search(plse_handle h, const uint8_t *S_in, uint8_t *S_out, int c
  * allocate device memory at call time (an application whose device memory is
  * reserved up front by its own pool allocator, or a latency-critical loop that
  * must not pay the implicit device-wide synchronisation of cudaMalloc/cudaFree).
- * The paper has no counterpart: it is a deployment variant of Alg. 3.  Same
+ * The paper has no counterpart: this is a deployment variant only.  Same
  * arguments, outputs and results as plse_local_search; it calls no cudaMalloc,
  * cudaFree or allocating routine.  Its scratch is a fixed 16 MiB array inside
- * the library on every GPU that loads it (held until exit), which bounds the
- * concurrent walks to (16 MiB - 256 B) / (4*|V|*n1p + 4) (n1p = n + 1 rounded up
- * to a multiple of 4): fewer walks in flight than plse_local_search uses on
- * large instances, same results.  PLSE_ENOTSUP if not even one walk fits.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Calls share
- * the array: each clears the part it uses, and calls whose work overlaps on the
- * GPU (e.g. on two streams) race.  Device-side check failures of this entry
- * point are recorded in the array, not reported by plse_sync. */
+ * the library on every GPU that loads it (held until exit).  Each concurrent
+ * walk needs 4*|V|*n1p + 10*|V| + 4*n*n1p + 64*n*cw + 4 bytes of it
+ * (n1p = n + 1 rounded up to a multiple of 4, cw = 32-colour words of n + 1
+ * colours), so fewer walks run at once than in plse_local_search on large
+ * instances (15 at n = 70, r = 0.3), with the same results.  PLSE_ENOTSUP if
+ * not even one walk fits.  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  Calls share the array: each clears the part it uses, and
+ * calls whose work overlaps on the GPU (e.g. on two streams) race.  A failed
+ * device-side check is reported as PLSE_ECHECK by plse_sync on the calling
+ * handle, as for plse_local_search, provided that no later call of this entry
+ * point (which clears the flag) was made first. */
 int  plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uint8_t *S_out, int count,
                                int ind0, int gen, int64_t iters, uint64_t seed, int flags,
                                int32_t *f_out, int64_t *F_out, plse_walk_stats *stats,

@@ -427,15 +427,23 @@ int plse_sync(plse_handle h, void *stream)
     if (!h) return PLSE_EINVAL;
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "plse_sync");
-    if (!h->ws.counters) return PLSE_OK;
-    int flag = 0;
-    e = cudaMemcpy(&flag, h->ws.counters + 1, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(h, e, "plse_sync");
-    if (flag) {
-        cudaMemsetAsync(h->ws.counters + 1, 0, sizeof(int), (cudaStream_t)stream);
-        cudaStreamSynchronize((cudaStream_t)stream);
-        return fail(h, PLSE_ECHECK, "a device-side consistency check failed (flag %d)", flag);
+    // the flag of the handle's own workspace, then that of its last call of
+    // plse_local_search_noalloc (a word of the library's fixed scratch array)
+    int *flags[2] = {h->ws.counters ? h->ws.counters + 1 : nullptr, h->noalloc_flag};
+    h->noalloc_flag = nullptr;
+    int failed = 0;
+    for (int *fp : flags) {
+        if (!fp) continue;
+        int flag = 0;
+        e = cudaMemcpy(&flag, fp, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "plse_sync");
+        if (flag) {
+            cudaMemsetAsync(fp, 0, sizeof(int), (cudaStream_t)stream);
+            cudaStreamSynchronize((cudaStream_t)stream);
+            failed = flag;
+        }
     }
+    if (failed) return fail(h, PLSE_ECHECK, "a device-side consistency check failed (flag %d)", failed);
     return PLSE_OK;
 }
 

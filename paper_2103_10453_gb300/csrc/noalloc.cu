@@ -19,6 +19,9 @@
 // call shares the one array and leaves its contents behind, so each call clears
 // the part it uses before its kernel runs; calls whose work overlaps on the GPU
 // (e.g. on two streams) race on the array and give unspecified results.
+// A failed device-side check is recorded in the array's flag word; plse_sync on
+// the calling handle reads it (and clears it) like the flag of
+// plse_local_search, until the next call of this entry point clears it.
 #include <algorithm>
 #include <mutex>
 
@@ -158,5 +161,6 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     a.skip = nullptr;
     e = launch_local_search(h->di, a, L, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "plse_local_search_noalloc: launch");
+    h->noalloc_flag = counters + 1;    // plse_sync reads (and clears) it
     return PLSE_OK;
 }

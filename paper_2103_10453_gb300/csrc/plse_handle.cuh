@@ -68,6 +68,8 @@ struct plse_instance {
     uint32_t *step_planes = nullptr;   // bit planes for the population step entry points
     size_t step_planes_cap = 0;
     plse::PopScratch step_ps;          // Alg. 4 scratch for plse_pop_update
+    int *noalloc_flag = nullptr;       // check flag of the last plse_local_search_noalloc call (in
+                                       // the library's fixed scratch array), read by plse_sync
     cudaEvent_t done_ev = nullptr;     // recorded after the handle's latest enqueued work
     bool done_recorded = false;
     std::string err;
