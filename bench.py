@@ -48,6 +48,9 @@ def parse():
                          "search on the n=70 instance with fill ratio R (population --pop, "
                          "--ls-iters iterations per launch, --steps launches)")
     ap.add_argument("--ls-iters", type=int, default=3000)
+    ap.add_argument("--launch", default=None, metavar="LANES,WALKS,PLACE",
+                    help="local-search launch knobs for every instance (plse_set_launch): threads "
+                         "per walk, walks per block, colouring placement; results do not change")
     ap.add_argument("--batch", action="store_true",
                     help="batching case instead of the benchmark: 64 uneven instances solved one "
                          "by one with plse_solve, then together with plse_solve_batch")
@@ -206,6 +209,8 @@ def run_gpu(args):
         G = plse.Instance(g)
         prm = plse.default_params(stop_at_bound=0)
         G.set_params(prm)
+        if args.launch:
+            G.set_launch(*[int(x) for x in args.launch.split(",")])
         G.run_begin(args.pop, args.warmup + args.steps + 1, 10 * G.nv, seed)
         insts.append(G)
 
@@ -414,6 +419,8 @@ def run_ls_case(args):
     import torch
     from paper_2103_10453_gb300 import inputs, plse
     G = plse.Instance(inputs.n70(args.ls_case))
+    if args.launch:
+        G.set_launch(*[int(x) for x in args.launch.split(",")])
     pop = args.pop
     P = torch.empty((pop, G.nv), dtype=torch.uint8, device="cuda")
     Q = torch.empty_like(P)
@@ -437,7 +444,7 @@ def run_ls_case(args):
                      "pairs_per_iter": round(s[3] / max(s[0], 1), 2),
                      "bytes_alg": walk_bytes(dict(zip(["iterations", "moves", "cand", "pairs", "deg"], s)))})
     print(json.dumps({"case": "ls_steady", "n": 70, "r": args.ls_case, "nv": G.nv, "population": pop,
-                      "iters": args.ls_iters, "runs": runs}), flush=True)
+                      "iters": args.ls_iters, "launch": args.launch, "runs": runs}), flush=True)
     G.close()
 
 

@@ -122,10 +122,47 @@ void plse_default_params(plse_params *p);
 int  plse_set_params(plse_handle h, const plse_params *p);
 int  plse_get_params(plse_handle h, plse_params *p);
 
-/* Launch knobs that never change results: warps per walk of the local-search
- * kernel (1, 2, 4 or 8; 0 = automatic) and the cap on concurrent walks per block
- * (0 = as many as fit in shared memory). */
-int  plse_set_launch(plse_handle h, int ls_warps, int ls_walks);
+/* Launch knobs of the local-search kernel; they never change results.
+ * ls_lanes: threads per walk, 16 (two walks share a warp), 32, 64, 128 or 256;
+ * 0 = automatic.  ls_walks: cap on concurrent walks per block (0 = as many as
+ * fit).  ls_colourings: where a walk's current colouring lives, 1 = shared
+ * memory, 2 = global memory (frees shared memory for more walks), 0 =
+ * automatic (shared memory unless that would cut the walks per block). */
+int  plse_set_launch(plse_handle h, int ls_lanes, int ls_walks, int ls_colourings);
+
+/* plse_autotune -- picks the launch knobs above for runs of `pop` individuals
+ * on this handle's instance by timing short probe launches of the local search
+ * (`probe_iters` phase-1 iterations on `pop` colourings, several candidate
+ * shapes: threads per walk, walks per block, colouring placement), applies the
+ * fastest to the handle and reports it (each output may be NULL; moves_per_s is
+ * the probe's rate).  The choice is cached for the process per device, n, |V|
+ * and pop, so later calls for the same shape return at once.  Results of every
+ * call never depend on the knobs.  Uses device memory for two probe
+ * populations (from the handle's allocator: its bound workspace, if any) and
+ * waits for the device. */
+int  plse_autotune(plse_handle h, int pop, int probe_iters, int *lanes, int *walks, int *colourings,
+                   double *moves_per_s);
+
+/* ---- caller-supplied device memory -------------------------------------------
+ * plse_workspace_size: device bytes that a run of `pop` individuals and up to
+ * `max_generations` generations (plse_run_begin / plse_solve) takes for its
+ * population buffers, Alg. 4 scratch and local-search scratch, under the
+ * handle's current parameters and launch knobs (0 for an instance with no
+ * vertex left to colour).
+ * plse_bind_workspace: from now on the handle carves those buffers (and the
+ * scratch of the step entry points) out of the device range
+ * [dev_ptr, dev_ptr + bytes) instead of the library's pool; e.g. a torch
+ * tensor's memory.  The range is caller-owned: it must start on a 256-byte
+ * boundary, be memory of the handle's device, and stay valid until it is
+ * unbound, another is bound or the handle is destroyed.  The call waits for the
+ * handle's work, releases its current buffers and discards its current run
+ * (begin a new one).  Pieces are never returned to the range one by one: a
+ * later call that needs more than is left (a larger run, more step scratch)
+ * fails with PLSE_ENOMEM.  dev_ptr = NULL unbinds (buffers come from the pool
+ * again).  The instance image uploaded by plse_create stays in the pool.
+ * Results do not depend on where the memory comes from. */
+int  plse_workspace_size(plse_handle h, int pop, int max_generations, size_t *bytes);
+int  plse_bind_workspace(plse_handle h, void *dev_ptr, size_t bytes);
 
 /* ---- whole solve (Alg. 2) ---------------------------------------------------
  * Runs `generations` generations of MPMA with population `pop` (2..65535) and
@@ -157,6 +194,16 @@ int  plse_run_begin(plse_handle h, int pop, int max_generations, int64_t iters, 
 int  plse_run_step(plse_handle h, int generations, void *stream, int *done);
 int  plse_run_result(plse_handle h, void *stream, int8_t *best_grid, int *best_score,
                      plse_solve_stats *stats, int32_t *trace);
+
+/* plse_run_population -- copies the run's current population P_t
+ * (which = PLSE_RUN_POPULATION) or the offspring S^O that the next generation's
+ * local search starts from (PLSE_RUN_OFFSPRING) into dst (device or host
+ * uint8 [pop*nv]); waits for the run's generations in flight and for the copy.
+ * The next generation (index = generations completed) runs plse_local_search
+ * on S^O with ind0 = 0, gen = that index and the run's iters and seed. */
+#define PLSE_RUN_POPULATION 0
+#define PLSE_RUN_OFFSPRING  1
+int  plse_run_population(plse_handle h, int which, uint8_t *dst, void *stream);
 
 /* Non-blocking form of plse_run_step, for callers that drive several runs from
  * one host thread (each run on its own stream, so their kernels overlap).
@@ -190,12 +237,21 @@ typedef struct {
     double  ms_queue;         /* host wall time from submission to the start    */
     double  ms_wall;          /* host wall time from submission to completion   */
     char    detail[128];      /* message of the job's error ("" on success)     */
+    int64_t mem_bytes;        /* server: device bytes the request was admitted
+                                 with (instance image + plse_workspace_size)    */
 } plse_result;
 
 /* plse_solve_batch -- runs job i on handle hs[i] (with that handle's
- * parameters), up to `max_inflight` jobs at a time (0 = 16), each on its own
- * stream, with their kernels overlapping on the current device; jobs naming the
- * same handle run one after another.  best_grids (may be NULL, entries may be
+ * parameters).  With max_inflight = 0 and a handle of its own for every job,
+ * all runs advance one generation at a time and the local searches of a
+ * generation run as one persistent launch per colour-word class (orders n
+ * below 32, 64, 96, 128), which takes the runs' walks in turn so that one run's
+ * tail is filled with the next run's walks; the rest of each generation runs on
+ * the run's own stream; a class whose first handle has automatic launch knobs
+ * gets them from plse_autotune on its largest instance.  Otherwise up to
+ * `max_inflight` jobs run at a time
+ * (0 = 16), each on its own stream, with their kernels overlapping on the
+ * current device, and jobs naming the same handle run one after another.  best_grids (may be NULL, entries may be
  * NULL): host int8 [n_i*n_i] outputs as plse_solve.  results: host [count].
  * Every job's result equals that of plse_solve with the same arguments.
  * Blocks until every job is done; returns the first job error (in index order)
@@ -204,10 +260,17 @@ int  plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count, int max_
                       int8_t *const *best_grids, plse_result *results);
 
 /* Request server: a host thread of the library that admits submitted requests
- * (grid + job + parameters) into `max_inflight` concurrent runs on the device
- * that is current at plse_server_create, in arrival order, and keeps each
- * result until it is polled.  Per-request results are identical to plse_solve
- * of the same request alone (the job's size never depends on load).
+ * (grid + job + parameters) into at most `max_inflight` concurrent runs on the
+ * device that is current at plse_server_create, in arrival order, and keeps
+ * each result until it is polled.  Admission is by device memory: the request
+ * at the head of the queue has its handle built (host work and the small
+ * instance upload), its footprint computed (instance image + plse_workspace_size
+ * of its run), and starts once a run slot is free and the footprint fits in
+ * `mem_budget` minus the footprints of the runs in progress (0 = 90% of the
+ * device memory free at creation); a run's bytes return to the budget when it
+ * completes.  A request whose footprint alone exceeds the budget completes with
+ * PLSE_ENOMEM.  Per-request results are identical to plse_solve of the same
+ * request alone (the job's size never depends on load).
  *   submit: copies `grid` (n*n) and `params` (NULL = defaults); returns a
  *     ticket, or PLSE_EBUSY when `max_queue` requests already wait (admission
  *     refused; nothing is queued), PLSE_EINVAL for a malformed request (grids
@@ -220,20 +283,25 @@ int  plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count, int max_
  *     a running one stops enqueueing generations and completes with
  *     PLSE_ECANCELLED and its best so far once its generations in flight end.
  *   pending: requests waiting for admission and results not yet polled.
+ *   memory: the budget, bytes held by running requests now, the peak of that,
+ *     the peak number of concurrent runs, and how many admissions had to wait
+ *     for memory (each output may be NULL).
  *   destroy: cancels what is waiting or running, joins the threads, frees all.
  * Every call except destroy may come from any host thread at any time; destroy
  * must not overlap another call on the same server. */
 typedef struct plse_server_s *plse_server;
-int  plse_server_create(int max_inflight, int max_queue, plse_server *out);
+int  plse_server_create(int max_inflight, int max_queue, size_t mem_budget, plse_server *out);
 int  plse_server_submit(plse_server s, int n, const int8_t *grid, const plse_job *job,
                         const plse_params *params, int64_t *ticket);
 int  plse_server_poll(plse_server s, int64_t ticket, int wait_ms, int8_t *best_grid,
                       plse_result *out);
 int  plse_server_cancel(plse_server s, int64_t ticket);
 int  plse_server_pending(plse_server s, int *queued, int *completed);
+int  plse_server_memory(plse_server s, size_t *budget, size_t *in_use, size_t *peak, int *peak_running,
+                        int64_t *waited);
 /* Launch knobs (as plse_set_launch) for the handles of requests admitted from
  * now on; they never change results. */
-int  plse_server_set_launch(plse_server s, int ls_warps, int ls_walks);
+int  plse_server_set_launch(plse_server s, int ls_lanes, int ls_walks, int ls_colourings);
 void plse_server_destroy(plse_server s);
 
 /* ---- step entry points (device buffers, asynchronous on `stream`) ---------

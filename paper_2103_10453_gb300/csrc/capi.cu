@@ -125,6 +125,7 @@ int upload_instance(plse_instance *h)
     const size_t o_ac = off; off = up256(off + 16 * (size_t)n);
     cudaError_t e = dev_malloc(&h->inst_mem, off, cudaStreamLegacy);
     if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "instance upload: %s", cudaGetErrorString(e));
+    h->inst_bytes = off;
     std::vector<uint8_t> img(off, 0);
     if (nv) {
         memcpy(img.data() + o_rc, h->rc.data(), 2 * (size_t)nv);
@@ -212,9 +213,9 @@ template <typename T>
 static int grow(plse_instance *h, T *&ptr, size_t &cap, size_t need, bool zero, cudaStream_t st)
 {
     if (need <= cap) return PLSE_OK;
-    if (ptr) { dev_free(ptr, st); ptr = nullptr; cap = 0; }
+    if (ptr) { h_free(h, ptr, st); ptr = nullptr; cap = 0; }
     void *q = nullptr;
-    cudaError_t e = dev_malloc(&q, need * sizeof(T), st);
+    cudaError_t e = h_malloc(h, &q, need * sizeof(T), st);
     if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "workspace: %s", cudaGetErrorString(e));
     ptr = static_cast<T *>(q);
     if (zero) {
@@ -223,6 +224,31 @@ static int grow(plse_instance *h, T *&ptr, size_t &cap, size_t need, bool zero, 
     }
     cap = need;
     return PLSE_OK;
+}
+
+void release_ls_workspace(plse_instance *h, cudaStream_t st)
+{
+    Workspace &ws = h->ws;
+    h_free(h, ws.G, st);
+    h_free(h, ws.TC, st);
+    h_free(h, ws.LIST, st);
+    h_free(h, ws.XR, st);
+    h_free(h, ws.HP, st);
+    h_free(h, ws.SW, st);
+    h_free(h, ws.slot_clock, st);
+    h_free(h, ws.counters, st);
+    ws = Workspace();
+}
+
+// Device bytes ensure_ls_workspace takes for `slots` walk slots, each buffer
+// rounded up as the bound-workspace allocator does.
+size_t ls_workspace_bytes(const plse_instance *h, int slots)
+{
+    const DevInst &I = h->di;
+    const size_t s = (size_t)slots;
+    return ws_align(4 * s * I.nv * I.n1p) + ws_align(8 * s * I.nv) + ws_align(2 * s * I.nv) +
+           ws_align(2 * s * 2 * I.n * I.n1p) + ws_align(4 * s * hp_words(I)) + ws_align(s * sw_bytes(I)) +
+           ws_align(4 * s) + ws_align(4 * 8);
 }
 
 int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
@@ -243,17 +269,18 @@ int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
     if (rc) return rc;
     rc = grow(h, ws.HP, ws.HP_cap, (size_t)slots * hp_words(h->di), false, st);          // idem
     if (rc) return rc;
+    rc = grow(h, ws.SW, ws.SW_cap, (size_t)slots * sw_bytes(h->di), false, st);          // idem
+    if (rc) return rc;
     rc = grow(h, ws.slot_clock, ws.clock_cap, (size_t)slots, true, st);
     if (rc) return rc;
     return grow(h, ws.counters, ws.counters_cap, 8, true, st);
 }
 
-int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
-                         int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
-                         int64_t *F_out, plse_walk_stats *stats, cudaStream_t st, const int *skip)
+LSArgs ls_args(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0, int gen, int64_t iters,
+               uint64_t seed, int flags, int32_t *f_out, int64_t *F_out, plse_walk_stats *stats, const int *skip)
 {
     const plse_params &p = h->params;
-    LSArgs a;
+    LSArgs a{};
     a.S_in = S_in;
     a.S_out = S_out;
     a.count = count;
@@ -277,18 +304,28 @@ int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, 
     a.F_out = F_out;
     a.stats = stats;
     a.skip = skip;
-    LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_warps, h->ls_walks);
+    const Workspace &ws = h->ws;
+    a.G = ws.G;
+    a.TC = ws.TC;
+    a.LIST = ws.LIST;
+    a.XR = ws.XR;
+    a.HP = ws.HP;
+    a.SW = ws.SW;
+    a.slot_clock = ws.slot_clock;
+    a.work_counter = ws.counters;
+    a.error_flag = ws.counters ? ws.counters + 1 : nullptr;
+    return a;
+}
+
+int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
+                         int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
+                         int64_t *F_out, plse_walk_stats *stats, cudaStream_t st, const int *skip)
+{
+    LSLaunch L = plan_local_search(h->di, h->device, count, h->ls_lanes, h->ls_walks, h->ls_splace);
     if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "local search does not fit on this device");
     int rc = ensure_ls_workspace(h, L.slots(), st);
     if (rc) return rc;
-    a.G = h->ws.G;
-    a.TC = h->ws.TC;
-    a.LIST = h->ws.LIST;
-    a.XR = h->ws.XR;
-    a.HP = h->ws.HP;
-    a.slot_clock = h->ws.slot_clock;
-    a.work_counter = h->ws.counters;
-    a.error_flag = h->ws.counters + 1;
+    const LSArgs a = ls_args(h, S_in, S_out, count, ind0, gen, iters, seed, flags, f_out, F_out, stats, skip);
     cudaError_t e = cudaMemsetAsync(a.work_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "local search");
     e = launch_local_search(h->di, a, L, st);
@@ -365,14 +402,7 @@ void plse_destroy(plse_handle h)
     if (h->done_recorded) cudaStreamWaitEvent(st, h->done_ev, 0);
     release_solver(h, st);
     dev_free(h->inst_mem, st);
-    Workspace &ws = h->ws;
-    dev_free(ws.G, st);
-    dev_free(ws.TC, st);
-    dev_free(ws.LIST, st);
-    dev_free(ws.XR, st);
-    dev_free(ws.HP, st);
-    dev_free(ws.slot_clock, st);
-    dev_free(ws.counters, st);
+    release_ls_workspace(h, st);
     if (h->done_ev) cudaEventDestroy(h->done_ev);
     delete h;
 }
@@ -412,13 +442,57 @@ int plse_get_params(plse_handle h, plse_params *p)
     return PLSE_OK;
 }
 
-int plse_set_launch(plse_handle h, int ls_warps, int ls_walks)
+int plse_set_launch(plse_handle h, int ls_lanes, int ls_walks, int ls_colourings)
 {
-    if (!h || !(ls_warps == 0 || ls_warps == 1 || ls_warps == 2 || ls_warps == 4 || ls_warps == 8) ||
-        ls_walks < 0 || ls_walks > 256)
+    if (!h || !(ls_lanes == 0 || ls_lanes == 16 || ls_lanes == 32 || ls_lanes == 64 || ls_lanes == 128 ||
+                ls_lanes == 256) ||
+        ls_walks < 0 || ls_walks > 256 || ls_colourings < 0 || ls_colourings > 2)
         return PLSE_EINVAL;
-    h->ls_warps = ls_warps;
+    h->ls_lanes = ls_lanes;
     h->ls_walks = ls_walks;
+    h->ls_splace = ls_colourings;
+    return PLSE_OK;
+}
+
+int plse_workspace_size(plse_handle h, int pop, int max_generations, size_t *bytes)
+{
+    if (!h || !bytes || pop < 2 || pop > 65535 || max_generations < 0 || max_generations > 65534)
+        return PLSE_EINVAL;
+    *bytes = 0;
+    if (h->nv == 0) return PLSE_OK;
+    const LSLaunch L = plan_local_search(h->di, h->device, pop, h->ls_lanes, h->ls_walks, h->ls_splace);
+    if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "local search does not fit on this device");
+    *bytes = solver_bytes(h, pop, max_generations) + ls_workspace_bytes(h, L.slots());
+    return PLSE_OK;
+}
+
+int plse_bind_workspace(plse_handle h, void *dev_ptr, size_t bytes)
+{
+    if (!h) return PLSE_EINVAL;
+    if (dev_ptr) {
+        if (reinterpret_cast<uintptr_t>(dev_ptr) % kWsAlign != 0)
+            return fail(h, PLSE_EINVAL, "plse_bind_workspace: range must start on a %zu-byte boundary", kWsAlign);
+        cudaPointerAttributes at{};
+        const cudaError_t e = cudaPointerGetAttributes(&at, dev_ptr);
+        if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != h->device) {
+            cudaGetLastError();
+            return fail(h, PLSE_EINVAL, "plse_bind_workspace: not device memory of device %d", h->device);
+        }
+    }
+    int rc = run_drain(h);
+    if (rc) return rc;
+    if (h->done_recorded) {
+        const cudaError_t e = cudaEventSynchronize(h->done_ev);
+        if (e != cudaSuccess) return cuda_fail(h, e, "plse_bind_workspace");
+    }
+    // every run and scratch buffer leaves its old memory (the pool or the
+    // previous range); the next call that needs one takes it from the new range
+    release_solver(h, cudaStreamLegacy);
+    release_ls_workspace(h, cudaStreamLegacy);
+    h->session = Session();
+    h->arena = dev_ptr ? static_cast<char *>(dev_ptr) : nullptr;
+    h->arena_size = dev_ptr ? bytes : 0;
+    h->arena_used = 0;
     return PLSE_OK;
 }
 

@@ -74,6 +74,27 @@ void dev_free(void *p, cudaStream_t st)
     if (p) cudaFreeAsync(p, st);
 }
 
+cudaError_t h_malloc(plse_instance *h, void **p, size_t bytes, cudaStream_t st)
+{
+    if (!h->arena) return dev_malloc(p, bytes, st);
+    const size_t off = ws_align(h->arena_used), need = bytes ? bytes : 16;
+    if (off > h->arena_size || need > h->arena_size - off) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    *p = h->arena + off;
+    h->arena_used = off + need;
+    return cudaSuccess;
+}
+
+void h_free(plse_instance *h, void *p, cudaStream_t st)
+{
+    if (!p) return;
+    const char *q = static_cast<const char *>(p);
+    if (h->arena && q >= h->arena && q < h->arena + h->arena_size) return;   // part of the bound range
+    dev_free(p, st);
+}
+
 int *pinned_slot_get()
 {
     std::lock_guard<std::mutex> lk(g_pinned_mutex);

@@ -11,6 +11,12 @@
 // filled by another's.  Per-job results are a function of the job alone (its
 // instance, parameters, pop, generations, iters and seed), never of the mix,
 // because no device state is shared between handles.
+//
+// The server admits requests in arrival order by device memory: a request's
+// footprint (its instance image plus plse_workspace_size of its run) is known
+// once its handle is built on the host, and the request at the head of the
+// queue starts when a stream slot is free and the footprint fits in the budget
+// left by the requests running; the bytes return to the budget when it ends.
 #include <chrono>
 #include <cstdio>
 #include <condition_variable>
@@ -85,6 +91,167 @@ bool advance(Active &a, bool &progressed)
     return true;
 }
 
+// plse_solve_batch when every job has a handle of its own: the runs advance one
+// generation at a time, and the local searches of a generation run as one
+// persistent multi-instance launch per colour-word class (instances that share a
+// kernel), each on a stream of its own; the rest of each run's generation runs
+// on the run's stream, overlapping with the other runs'.  Per-run results are
+// those of plse_solve: every kernel sees the same arguments as in a run alone.
+// Returns PLSE_ENOTSUP (nothing started) when a class has no launch that fits.
+int batch_lockstep(plse_instance **hs, const plse_job *jobs, int count, int8_t *const *grids,
+                   plse_result *results, Clock::time_point t0)
+{
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return PLSE_ECUDA;
+    // one launch plan per colour-word class, fixed for the whole batch
+    constexpr int kClasses = 4;
+    std::vector<int> cls(count);
+    std::vector<std::vector<int>> members(kClasses);
+    for (int i = 0; i < count; ++i) {
+        cls[i] = colour_words(hs[i]->n) - 1;
+        if (hs[i]->nv > 0 && job_valid(jobs[i])) members[cls[i]].push_back(i);
+    }
+    LSLaunch plan[kClasses];
+    int base[kClasses];                  // first entry of each class in the job tables
+    for (int c = 0, b = 0; c < kClasses; ++c) {
+        base[c] = b;
+        b += (int)members[c].size();
+    }
+    for (int c = 0; c < kClasses; ++c) {
+        if (members[c].empty()) continue;
+        std::vector<DevInst> insts;
+        for (int i : members[c]) insts.push_back(hs[i]->di);
+        plse_instance *h0 = hs[members[c][0]];
+        if (!h0->ls_lanes && !h0->ls_walks && !h0->ls_splace) {
+            // knobs of the class from its largest instance at its population
+            int big = members[c][0];
+            for (int i : members[c])
+                if (hs[i]->nv > hs[big]->nv) big = i;
+            int l = 0, w = 0, pl = 0;
+            if (plse_autotune(hs[big], jobs[big].pop, std::min(200, 2 * hs[big]->nv + 1), &l, &w, &pl,
+                              nullptr) == PLSE_OK) {
+                h0->ls_lanes = l;
+                h0->ls_walks = w;
+                h0->ls_splace = pl;
+            }
+        }
+        plan[c] = plan_local_search_multi(insts.data(), (int)insts.size(), device, h0->ls_lanes, h0->ls_walks,
+                                          h0->ls_splace);
+        if (plan[c].blocks <= 0) return PLSE_ENOTSUP;
+    }
+    std::vector<cudaStream_t> st(count, nullptr), cst(kClasses, nullptr);
+    std::vector<cudaEvent_t> cev(kClasses, nullptr);
+    LSJob *htab = nullptr, *dtab = nullptr;
+    int rc = PLSE_OK;
+    auto cleanup = [&]() {
+        for (auto &q : st) if (q) { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
+        for (auto &q : cst) if (q) { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
+        for (auto &e : cev) if (e) cudaEventDestroy(e);
+        if (dtab) cudaFree(dtab);
+        if (htab) cudaFreeHost(htab);
+    };
+    for (auto &q : st)
+        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) rc = PLSE_ECUDA;
+    for (int c = 0; c < kClasses; ++c)
+        if (cudaStreamCreateWithFlags(&cst[c], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&cev[c], cudaEventDisableTiming) != cudaSuccess)
+            rc = PLSE_ECUDA;
+    if (!rc && (cudaMallocHost(reinterpret_cast<void **>(&htab), sizeof(LSJob) * count) != cudaSuccess ||
+                cudaMalloc(reinterpret_cast<void **>(&dtab), sizeof(LSJob) * count) != cudaSuccess))
+        rc = PLSE_ENOMEM;
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    std::vector<char> live(count, 0);
+    for (int i = 0; i < count; ++i) {
+        plse_result &r = results[i];
+        r.ms_queue = ms_between(t0, Clock::now());
+        if (!job_valid(jobs[i])) {
+            r.status = fail(hs[i], PLSE_EINVAL, "plse_solve_batch: invalid job %d", i);
+            note_detail(r, hs[i]);
+            continue;
+        }
+        const int e = run_begin(hs[i], jobs[i].pop, jobs[i].generations, jobs[i].iters, jobs[i].seed, st[i]);
+        if (e) {
+            r.status = e;
+            note_detail(r, hs[i]);
+            continue;
+        }
+        r.status = PLSE_OK;
+        live[i] = 1;
+    }
+    auto can_issue = [&](int i) {
+        const Session &se = hs[i]->session;
+        return live[i] && se.active && !se.finished && se.issued < se.max_gens && hs[i]->solver;
+    };
+    for (;;) {
+        bool any = false;
+        for (int c = 0; c < kClasses; ++c) {
+            std::vector<int> idx;
+            for (int i : members[c])
+                if (can_issue(i)) idx.push_back(i);
+            if (idx.empty()) continue;
+            any = true;
+            std::vector<int> ok;
+            for (int i : idx) {
+                LSArgs a;
+                cudaEvent_t ready = nullptr;
+                const int e = generation_head(hs[i], plan[c].slots(), a, &ready);
+                if (e) {
+                    results[i].status = e;
+                    note_detail(results[i], hs[i]);
+                    live[i] = 0;
+                    continue;
+                }
+                htab[base[c] + (int)ok.size()] = LSJob{hs[i]->di, a};
+                cudaStreamWaitEvent(cst[c], ready, 0);
+                ok.push_back(i);
+            }
+            if (ok.empty()) continue;
+            const int off = base[c];
+            cudaError_t e = cudaMemcpyAsync(dtab + off, htab + off, sizeof(LSJob) * ok.size(),
+                                            cudaMemcpyHostToDevice, cst[c]);
+            if (e == cudaSuccess) e = launch_local_search_multi(dtab + off, (int)ok.size(), plan[c], cst[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(cev[c], cst[c]);
+            for (int i : ok) {
+                const int t = e == cudaSuccess ? generation_tail(hs[i], cev[c]) : cuda_fail(hs[i], e, "batched launch");
+                if (t) {
+                    results[i].status = t;
+                    note_detail(results[i], hs[i]);
+                    live[i] = 0;
+                }
+            }
+        }
+        if (!any) break;
+        // the generation of every run completes before the table is refilled
+        for (int i = 0; i < count; ++i) {
+            if (!live[i]) continue;
+            const int e = run_poll(hs[i], true);
+            if (e) {
+                results[i].status = e;
+                note_detail(results[i], hs[i]);
+                live[i] = 0;
+            }
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        plse_result &r = results[i];
+        if (live[i]) {
+            const int e = run_result(hs[i], st[i], grids ? grids[i] : nullptr, &r.best_score, &r.stats, nullptr);
+            r.status = e;
+            if (e) note_detail(r, hs[i]);
+        }
+        if (hs[i]->session.active) {
+            cudaStreamSynchronize(st[i]);
+            hs[i]->session.active = 0;
+        }
+        r.ms_wall = ms_between(t0, Clock::now());
+    }
+    cleanup();
+    return PLSE_OK;
+}
+
 }  // namespace
 }  // namespace plse
 
@@ -103,6 +270,21 @@ extern "C" int plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count
     for (int i = 0; i < count; ++i) {
         memset(&results[i], 0, sizeof(plse_result));
         results[i].status = PLSE_EINVAL;
+    }
+    // every job on a handle of its own and no cap on runs in flight: one
+    // multi-instance local-search launch per generation and colour-word class
+    bool distinct = max_inflight == 0;
+    if (distinct) {
+        std::unordered_set<plse_instance *> seen;
+        for (int i = 0; i < count; ++i) distinct = distinct && seen.insert(hs[i]).second;
+    }
+    if (distinct) {
+        const int rc = batch_lockstep(hs, jobs, count, best_grids, results, t0);
+        if (rc != PLSE_ENOTSUP) {
+            int first = rc;
+            for (int i = 0; i < count && !first; ++i) first = results[i].status;
+            return first;
+        }
     }
     const int slots = std::max(1, std::min(count, max_inflight > 0 ? max_inflight : 16));
     std::vector<cudaStream_t> streams(slots, nullptr);
@@ -193,11 +375,16 @@ struct plse_server_s {
         Active a;
         std::vector<int8_t> grid;
         plse_result res{};
+        size_t need = 0;          // bytes counted against the budget while it runs
     };
 
     int device = 0;
     int max_inflight = 0, max_queue = 0;
-    int ls_warps = 0, ls_walks = 0;     // launch knobs applied to every request's handle
+    size_t budget = 0, in_use = 0, peak = 0;   // device-memory admission (bytes)
+    int64_t waited_for_memory = 0;             // admissions that had to wait for memory
+    int running = 0, peak_running = 0;
+    int head_pending = 0;                      // a dequeued request waiting for a slot or memory
+    int ls_lanes = 0, ls_walks = 0, ls_colourings = 0;   // launch knobs of every request's handle
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request> queue;
@@ -216,6 +403,7 @@ struct plse_server_s {
     void finish(Running &r)
     {
         Done d;
+        r.res.mem_bytes = (int64_t)r.need;
         d.res = r.res;
         d.res.ms_wall = ms_between(r.req.arrival, Clock::now());
         d.grid = std::move(r.grid);
@@ -223,6 +411,11 @@ struct plse_server_s {
             std::lock_guard<std::mutex> lk(mu);
             cancel_running.erase(r.req.ticket);
             done.emplace(r.req.ticket, std::move(d));
+            if (r.need) {
+                in_use -= r.need;
+                --running;
+                r.need = 0;
+            }
         }
         cv_done.notify_all();
         if (r.a.h) {
@@ -255,55 +448,113 @@ struct plse_server_s {
         for (auto &s : streams) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         std::vector<Running> slot(max_inflight);
         std::vector<char> used(max_inflight, 0);
+        Running head;                    // next request, handle built, waiting for a slot or memory
+        size_t head_need = 0;
+        bool head_ready = false, head_waited = false;
         for (;;) {
             bool progressed = false;
-            // admission
+            // admission: the request at the head of the queue gets its handle
+            // built (host work and the instance upload), then waits until a slot
+            // is free and its footprint fits in the memory budget
             for (int s = 0; s < max_inflight; ++s) {
                 if (used[s]) continue;
-                Request req;
-                {
-                    std::unique_lock<std::mutex> lk(mu);
-                    int busy = 0;
-                    for (char u : used) busy += u;
-                    if (queue.empty()) {
-                        if (stop) break;
-                        if (busy == 0) {
-                            cv_work.wait(lk, [&] { return stop || !queue.empty(); });
-                            if (queue.empty()) break;
-                        } else {
-                            break;
+                if (!head_ready) {
+                    Request req;
+                    {
+                        std::unique_lock<std::mutex> lk(mu);
+                        int busy = 0;
+                        for (char u : used) busy += u;
+                        if (queue.empty()) {
+                            if (stop) break;
+                            if (busy == 0) {
+                                cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+                                if (queue.empty()) break;
+                            } else {
+                                break;
+                            }
                         }
+                        req = std::move(queue.front());
+                        queue.pop_front();
                     }
-                    req = std::move(queue.front());
-                    queue.pop_front();
+                    progressed = true;
+                    head = Running();
+                    head.req = std::move(req);
+                    if (head.req.cancel) {
+                        head.res.ms_queue = ms_between(head.req.arrival, Clock::now());
+                        head.res.status = PLSE_ECANCELLED;
+                        note_detail(head.res, nullptr);
+                        finish(head);
+                        continue;
+                    }
+                    plse_instance *h = nullptr;
+                    int rc = plse_create(head.req.n, head.req.grid.data(), &h);
+                    if (!rc) rc = plse_set_params(h, &head.req.params);
+                    if (!rc) {
+                        std::lock_guard<std::mutex> lk(mu);
+                        rc = plse_set_launch(h, ls_lanes, ls_walks, ls_colourings);
+                    }
+                    size_t ws = 0;
+                    if (!rc) rc = plse_workspace_size(h, head.req.job.pop, head.req.job.generations, &ws);
+                    head.grid.assign((size_t)head.req.n * head.req.n, 0);
+                    head.a = Active{h, nullptr, head.grid.data(), &head.res, false};
+                    head_need = (h ? h->inst_bytes : 0) + ws;
+                    if (!rc && head_need > budget)
+                        rc = h ? fail(h, PLSE_ENOMEM, "request needs %zu bytes of device memory, the server's "
+                                      "budget is %zu", head_need, budget) : PLSE_ENOMEM;
+                    if (rc) {
+                        head.res.ms_queue = ms_between(head.req.arrival, Clock::now());
+                        head.res.status = rc;
+                        note_detail(head.res, h);
+                        finish(head);
+                        continue;
+                    }
+                    head_ready = true;
+                    std::lock_guard<std::mutex> lk(mu);
+                    head_pending = 1;
+                }
+                bool cancelled = false, fits = false;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    cancelled = stop || cancel_running.count(head.req.ticket) != 0;
+                    fits = in_use + head_need <= budget;
+                    if (cancelled || fits) head_pending = 0;
+                    if (!cancelled && fits) {
+                        in_use += head_need;
+                        peak = std::max(peak, in_use);
+                        ++running;
+                        peak_running = std::max(peak_running, running);
+                        if (head_waited) ++waited_for_memory;
+                    }
+                }
+                if (cancelled) {
+                    head.res.ms_queue = ms_between(head.req.arrival, Clock::now());
+                    head.res.status = PLSE_ECANCELLED;
+                    note_detail(head.res, nullptr);
+                    finish(head);
+                    head_ready = head_waited = false;
+                    progressed = true;
+                    continue;
+                }
+                if (!fits) {                      // wait for running requests to free memory
+                    head_waited = true;
+                    break;
                 }
                 progressed = true;
                 Running &r = slot[s];
-                r = Running();
-                r.req = std::move(req);
+                r = std::move(head);
+                head_ready = head_waited = false;
+                r.need = head_need;
                 r.res.ms_queue = ms_between(r.req.arrival, Clock::now());
-                if (r.req.cancel) {
-                    r.res.status = PLSE_ECANCELLED;
-                    note_detail(r.res, nullptr);
-                    finish(r);
-                    continue;
-                }
-                plse_instance *h = nullptr;
-                int rc = plse_create(r.req.n, r.req.grid.data(), &h);
-                if (!rc) rc = plse_set_params(h, &r.req.params);
-                if (!rc) {
-                    std::lock_guard<std::mutex> lk(mu);
-                    rc = plse_set_launch(h, ls_warps, ls_walks);
-                }
-                if (!rc) rc = run_begin(h, r.req.job.pop, r.req.job.generations, r.req.job.iters, r.req.job.seed,
-                                        streams[s]);
-                r.grid.assign((size_t)r.req.n * r.req.n, 0);
-                r.a = Active{h, streams[s], r.grid.data(), &r.res, false};
+                r.a.st = streams[s];
+                r.a.grid_out = r.grid.data();
+                r.a.res = &r.res;
+                const int rc = run_begin(r.a.h, r.req.job.pop, r.req.job.generations, r.req.job.iters,
+                                         r.req.job.seed, streams[s]);
                 if (rc) {
                     r.res.status = rc;
-                    note_detail(r.res, h);
+                    note_detail(r.res, r.a.h);
                     cudaStreamSynchronize(streams[s]);
-                    if (h) h->session.active = 0;
+                    r.a.h->session.active = 0;
                     finish(r);
                     continue;
                 }
@@ -311,7 +562,7 @@ struct plse_server_s {
             }
             {
                 std::lock_guard<std::mutex> lk(mu);
-                bool any = false;
+                bool any = head_ready;
                 for (char u : used) any |= u != 0;
                 if (stop && !any && queue.empty()) break;
                 for (int s = 0; s < max_inflight; ++s)
@@ -332,7 +583,7 @@ struct plse_server_s {
 
 extern "C" {
 
-int plse_server_create(int max_inflight, int max_queue, plse_server *out)
+int plse_server_create(int max_inflight, int max_queue, size_t mem_budget, plse_server *out)
 {
     if (!out || max_inflight < 1 || max_inflight > 256 || max_queue < 0) return PLSE_EINVAL;
     plse_server_s *s = new (std::nothrow) plse_server_s();
@@ -341,6 +592,15 @@ int plse_server_create(int max_inflight, int max_queue, plse_server *out)
         delete s;
         return PLSE_ECUDA;
     }
+    if (mem_budget == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            delete s;
+            return PLSE_ECUDA;
+        }
+        mem_budget = free_b / 10 * 9;
+    }
+    s->budget = mem_budget;
     s->max_inflight = max_inflight;
     s->max_queue = max_queue;
     s->worker = std::thread([s] { s->worker_loop(); });
@@ -392,6 +652,19 @@ int plse_server_poll(plse_server s, int64_t ticket, int wait_ms, int8_t *best_gr
     return PLSE_OK;
 }
 
+int plse_server_memory(plse_server s, size_t *budget, size_t *in_use, size_t *peak, int *peak_running,
+                       int64_t *waited)
+{
+    if (!s) return PLSE_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (budget) *budget = s->budget;
+    if (in_use) *in_use = s->in_use;
+    if (peak) *peak = s->peak;
+    if (peak_running) *peak_running = s->peak_running;
+    if (waited) *waited = s->waited_for_memory;
+    return PLSE_OK;
+}
+
 int plse_server_cancel(plse_server s, int64_t ticket)
 {
     if (!s) return PLSE_EINVAL;
@@ -407,12 +680,13 @@ int plse_server_cancel(plse_server s, int64_t ticket)
     return PLSE_OK;
 }
 
-int plse_server_set_launch(plse_server s, int ls_warps, int ls_walks)
+int plse_server_set_launch(plse_server s, int ls_lanes, int ls_walks, int ls_colourings)
 {
-    if (!s || ls_warps < 0 || ls_walks < 0) return PLSE_EINVAL;
+    if (!s || ls_lanes < 0 || ls_walks < 0 || ls_colourings < 0 || ls_colourings > 2) return PLSE_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
-    s->ls_warps = ls_warps;
+    s->ls_lanes = ls_lanes;
     s->ls_walks = ls_walks;
+    s->ls_colourings = ls_colourings;
     return PLSE_OK;
 }
 
@@ -420,7 +694,7 @@ int plse_server_pending(plse_server s, int *queued, int *completed)
 {
     if (!s) return PLSE_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
-    if (queued) *queued = (int)s->queue.size();
+    if (queued) *queued = (int)s->queue.size() + s->head_pending;
     if (completed) *completed = (int)s->done.size();
     return PLSE_OK;
 }

@@ -3,11 +3,13 @@
 // greedy conflict removal, Sec. 3.7) for sm_103a.
 //
 // Design (GB300-first):
-//  * A walk is owned by a group of NW warps (NW = 1, 2, 4, 8).  A block holds
-//    W independent groups, each with its own shared-memory slot, plus one copy
-//    of the instance's vertex coordinates and colour masks shared by all of
-//    them.  Groups take walks from an atomic counter and never wait for each
-//    other; a group of one warp needs no block barrier at all.
+//  * A walk is owned by a group of GT threads: half a warp (GT = 16, two walks
+//    per warp), one warp (32) or 2, 4, 8 warps.  A block holds W independent
+//    groups, each with its own shared-memory slot, plus one copy of the
+//    instance's vertex coordinates and colour masks shared by all of them.
+//    Groups take walks from an atomic counter and never wait for each other; a
+//    group within one warp needs no block barrier at all (its collectives use
+//    the group's lane mask).
 //  * The gamma table of the incremental evaluation (Sec. 3.3) is held in
 //    factored form.  On a Latin-square graph the neighbours of v = (r, c) are
 //    exactly its row- and column-mates, so
@@ -22,12 +24,14 @@
 //    entries evicted while possibly live.  A vertex whose evicted entries have
 //    all expired never touches G.
 //  * The candidate set V0 u C(S) is a bitmask plus a persistent list of its
-//    members (stale entries are skipped and the list is rebuilt when half of it
-//    is stale).  A move changes the status of its own vertex and of row- and
-//    column-mates only, so no per-iteration compaction is needed.  The chosen
-//    move is the minimum of the key (2dF, (v - r) mod |V|, j): a total order, so
-//    the result does not depend on how candidates are split among threads.
-//  * The walk's best colouring S'* is kept in the output row in global memory.
+//    members, compacted during the scan.  A move changes the status of its own
+//    vertex and of row- and column-mates only.  The chosen move is the minimum of
+//    the key (2dF, (v - r) mod |V|, j): a total order, so the result does not
+//    depend on how candidates are split among threads.
+//  * The current colouring lives in the slot (shared memory) when the slots
+//    still fit, else in a per-slot global buffer (L1-cached), which lets twice
+//    as many walks share an SM.  The walk's best colouring S'* is kept in the
+//    output row in global memory.
 #include <algorithm>
 #include <climits>
 
@@ -66,41 +70,52 @@ __device__ __forceinline__ int tenure_div(const LSArgs &a, int x)
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// threads per block of the local search: one block per SM at n >= 64 with 16
-// one-warp walks (n < 96) or 12 (n >= 96, whose kernel needs more registers),
-// two blocks of 8 walks per SM below
+// threads per block of the local search: one block per SM at n >= 64 (512
+// threads for n < 96, 384 from 96, whose kernel needs more registers), two
+// blocks of 256 per SM below.  The register budget per thread follows from it.
+#ifndef PLSE_LS_THREADS_N64
+#define PLSE_LS_THREADS_N64 512
+#endif
 template <int NWC>
-constexpr int kMaxThreads = NWC == 3 ? 512 : NWC == 4 ? 384 : 256;
+constexpr int kMaxThreads = NWC == 3 ? PLSE_LS_THREADS_N64 : NWC == 4 ? 384 : 256;
 
-// colour counts per (line, 32-colour word) are bit planes: planes 0, 1 and the OR
-// of planes 2..6 (a count >= 4) in shared memory, planes 2..6 in global memory,
-// where they are touched only when a count crosses a multiple of 4
-constexpr int kLo = 4;    // shared words: plane 0, plane 1, high OR, pad
-constexpr int kHi = 8;    // global words: planes 2..6, pad
+// a walk group of GT threads: W lanes in each of its NW warps
+template <int GT>
+struct Grp {
+    static constexpr int W = GT < 32 ? GT : 32;
+    static constexpr int NW = GT < 32 ? 1 : GT / 32;
+};
 
-__host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps)
+// colour counts per (line, 32-colour word) are bit planes: planes 0 and 1 (a
+// uint2) and the OR of planes 2..6 (a count >= 4) in shared memory, planes 2..6
+// in global memory, where they are touched only when a count crosses a
+// multiple of 4
+constexpr int kHi = 8;    // global words per (line, colour word): planes 2..6, pad
+
+__host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps, bool s_smem)
 {
     const int cw = colour_words(I.n);
     SmemPlan p;
     p.inst = align16(align16(2 * (size_t)I.nv) + 32 * (size_t)I.n + 2 * (size_t)I.n);
     size_t o = 0;
-    p.off_S = o;      o = align16(o + (size_t)I.nv);
-    p.off_RP = o;     o += 4 * kLo * (size_t)I.n * cw;
-    p.off_KP = o;     o += 4 * kLo * (size_t)I.n * cw;
+    p.off_S = o;
+    if (s_smem) o = align16(o + (size_t)I.nv);
+    p.off_P01 = o;    o += 8 * 2 * (size_t)I.n * cw;
+    p.off_PH = o;     o += 4 * 2 * (size_t)I.n * cw;
     p.off_cmask = o;  o += 4 * (size_t)I.nw;
     p.off_lmask = o;  o += 4 * (size_t)I.nw;
     p.off_red = align16(o);
-    o = p.off_red;
     o = p.off_red + 8 * 2 * (size_t)warps + 4 * 2 * (size_t)warps + 4 * 16;
     p.slot = align16(o);
     return p;
 }
 
-// One walk's shared-memory slot.
+// One walk's slot.
 struct Slot {
-    uint8_t *S;                 // current colouring [nv]
-    uint32_t *RP, *KP;          // colour-count planes 0, 1 and high OR [n][cw][kLo] per row / column
-    uint32_t *RH, *KH;          // colour-count planes 2..6 [n][cw][kHi] per row / column, global
+    uint8_t *S;                 // current colouring [nv] (shared or global memory)
+    uint2 *P01;                 // colour-count planes 0, 1 [2n][cw] (rows, then columns)
+    uint32_t *PH;               // OR of planes 2..6 [2n][cw]
+    uint32_t *HP;               // planes 2..6 [2n][cw][kHi], global
     uint32_t *cmask;            // candidate bitmask [nw]
     uint32_t *lmask;            // vertices present in the candidate list [nw]
     uint16_t *list;             // candidate list (may hold stale entries) [nv], global memory
@@ -109,7 +124,8 @@ struct Slot {
                                 // x = e0 | e1 << 16, y = c0 | c1 << 8 | emax << 16
     unsigned long long *red;    // [2][NW] best key per warp (double-buffered)
     int *red_cnt;               // [2][NW] live candidates seen per warp
-    int *scal;                  // [16]: 0 list length, 4 |C(S)|, 5..6 PartialCol, 7 walk id, 8.. reductions
+    int *scal;                  // [16]: 0 list length, 2 counts >= 4, 4 |C(S)|, 5..6 move
+                                // scratch, 7 walk id, 8.. reductions
 };
 
 // Per-thread view: instance data, its slot and its place in the group.
@@ -118,44 +134,51 @@ struct Ctx {
     const uint4 *allow;         // [2n] allowed colours per row, then per column (shared)
     const uint8_t *linelen;     // [2n] reduced vertices per row, then per column (shared)
     Slot s;
+    int n;                      // order: line index of column c is n + c
     int cw;                     // colour words of the plane layout
     int g;                      // group (walk slot) within the block
     int gt;                     // thread index within the group
-    int lane, wg;               // lane, warp within the group
+    int lane;                   // lane within the warp
+    int gl;                     // lane within the group's part of the warp
+    int wg;                     // warp within the group
+    unsigned gm;                // the group's lanes within the warp
 };
 
-template <int NW>
+template <int GT>
 __device__ __forceinline__ void gsync(const Ctx &c)
 {
-    if (NW == 1) __syncwarp();
-    else asm volatile("bar.sync %0, %1;" ::"r"(c.g + 1), "r"(32 * NW) : "memory");
+    if (Grp<GT>::NW == 1) __syncwarp(c.gm);
+    else asm volatile("bar.sync %0, %1;" ::"r"(c.g + 1), "r"(GT) : "memory");
 }
 
-template <int NW>
-__device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I)
+template <int GT>
+__device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I, bool s_smem)
 {
-    const SmemPlan p = make_plan(I, NW);
+    const SmemPlan p = make_plan(I, Grp<GT>::NW, s_smem);
     Ctx c;
     c.rc = reinterpret_cast<const uint16_t *>(base);
     c.allow = reinterpret_cast<const uint4 *>(base + align16(2 * (size_t)I.nv));
     c.linelen = base + align16(2 * (size_t)I.nv) + 32 * (size_t)I.n;
-    c.g = threadIdx.x / (32 * NW);
-    c.gt = threadIdx.x % (32 * NW);
+    c.g = threadIdx.x / GT;
+    c.gt = threadIdx.x % GT;
     c.lane = threadIdx.x & 31;
+    c.gl = c.lane & (Grp<GT>::W - 1);
     c.wg = c.gt >> 5;
+    c.gm = Grp<GT>::W == 32 ? FULL : (((1u << Grp<GT>::W) - 1u) << (c.lane & ~(Grp<GT>::W - 1)));
     uint8_t *sb = base + p.inst + p.slot * c.g;
-    c.s.S = sb + p.off_S;
-    c.s.RP = reinterpret_cast<uint32_t *>(sb + p.off_RP);
-    c.s.KP = reinterpret_cast<uint32_t *>(sb + p.off_KP);
+    c.s.S = s_smem ? sb + p.off_S : nullptr;      // global buffer set once the slot is known
+    c.s.P01 = reinterpret_cast<uint2 *>(sb + p.off_P01);
+    c.s.PH = reinterpret_cast<uint32_t *>(sb + p.off_PH);
     c.s.cmask = reinterpret_cast<uint32_t *>(sb + p.off_cmask);
     c.s.lmask = reinterpret_cast<uint32_t *>(sb + p.off_lmask);
     c.s.list = nullptr;         // set once the walk slot is known
-    c.s.RH = c.s.KH = nullptr;
+    c.s.HP = nullptr;
     c.s.xr = nullptr;
-    c.s.tc = nullptr;           // set once the walk slot is known
+    c.s.tc = nullptr;
     c.s.red = reinterpret_cast<unsigned long long *>(sb + p.off_red);
-    c.s.red_cnt = reinterpret_cast<int *>(sb + p.off_red + 16 * NW);
-    c.s.scal = c.s.red_cnt + 2 * NW;
+    c.s.red_cnt = reinterpret_cast<int *>(sb + p.off_red + 16 * Grp<GT>::NW);
+    c.s.scal = c.s.red_cnt + 2 * Grp<GT>::NW;
+    c.n = I.n;
     c.cw = colour_words(I.n);
     return c;
 }
@@ -164,83 +187,75 @@ struct LaneStats {
     long long iterations, moves, cand, pairs, deg, improvements, uncolored;
 };
 
-template <int NW>
+template <int GT>
 __device__ __forceinline__ int gsum(int x, const Ctx &c)
 {
-    x = __reduce_add_sync(FULL, x);
-    if (NW == 1) return x;
-    gsync<NW>(c);
+    x = __reduce_add_sync(c.gm, x);
+    if (Grp<GT>::NW == 1) return x;
+    gsync<GT>(c);
     if (c.lane == 0) c.s.scal[8 + c.wg] = x;
-    gsync<NW>(c);
+    gsync<GT>(c);
     int t = 0;
 #pragma unroll
-    for (int k = 0; k < NW; ++k) t += c.s.scal[8 + k];
-    gsync<NW>(c);
+    for (int k = 0; k < Grp<GT>::NW; ++k) t += c.s.scal[8 + k];
+    gsync<GT>(c);
     return t;
 }
 
-template <int NW>
+template <int GT>
 __device__ __forceinline__ uint32_t gmax(uint32_t x, const Ctx &c)
 {
-    x = __reduce_max_sync(FULL, x);
-    if (NW == 1) return x;
-    gsync<NW>(c);
+    x = __reduce_max_sync(c.gm, x);
+    if (Grp<GT>::NW == 1) return x;
+    gsync<GT>(c);
     if (c.lane == 0) c.s.scal[8 + c.wg] = (int)x;
-    gsync<NW>(c);
+    gsync<GT>(c);
     uint32_t t = 0;
 #pragma unroll
-    for (int k = 0; k < NW; ++k) t = max(t, (uint32_t)c.s.scal[8 + k]);
-    gsync<NW>(c);
+    for (int k = 0; k < Grp<GT>::NW; ++k) t = max(t, (uint32_t)c.s.scal[8 + k]);
+    gsync<GT>(c);
     return t;
 }
 
-template <int NW>
+template <int GT>
 __device__ __forceinline__ long long gsum64(long long x, const Ctx &c)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-    if (NW == 1) return x;
-    gsync<NW>(c);
+    for (int o = Grp<GT>::W / 2; o > 0; o >>= 1) x += __shfl_xor_sync(c.gm, x, o, Grp<GT>::W);
+    if (Grp<GT>::NW == 1) return x;
+    gsync<GT>(c);
     if (c.lane == 0) c.s.red[c.wg] = (unsigned long long)x;
-    gsync<NW>(c);
+    gsync<GT>(c);
     long long t = 0;
 #pragma unroll
-    for (int k = 0; k < NW; ++k) t += (long long)c.s.red[k];
-    gsync<NW>(c);
+    for (int k = 0; k < Grp<GT>::NW; ++k) t += (long long)c.s.red[k];
+    gsync<GT>(c);
     return t;
 }
 
-template <int NW>
+template <int GT>
 __device__ __forceinline__ void gcopy(uint8_t *dst, const uint8_t *src, int n, const Ctx &c)
 {
-    for (int q = c.gt; q < n; q += 32 * NW) dst[q] = src[q];
+    for (int q = c.gt; q < n; q += GT) dst[q] = src[q];
 }
 
 // ---- colour-count planes ----------------------------------------------------
-__device__ __forceinline__ const uint32_t *line_planes(const uint32_t *P, int cw, int line)
+// Lines are numbered 0..n-1 for rows and n..2n-1 for columns.
+__device__ __forceinline__ size_t plane_word(const Ctx &c, int line, int k)
 {
-    return P + (size_t)line * cw * kLo;
+    return (size_t)line * c.cw + (k >> 5);
 }
 
-__device__ __forceinline__ uint4 *lo_word(const Ctx &c, int side, int line, int k)
+// +1 / -1 on count[line][k] (one thread per line at a time).  Returns the change
+// in the number of counts >= 4, which selects the evaluation path, and the
+// updated shared words (plane 0, plane 1, high OR) in *lo_out (may be null).
+__device__ __forceinline__ int count_step(const Ctx &c, int line, int k, bool inc, uint4 *lo_out = nullptr)
 {
-    return reinterpret_cast<uint4 *>(side ? c.s.KP : c.s.RP) + (size_t)line * c.cw + (k >> 5);
-}
-
-__device__ __forceinline__ uint32_t *hi_words(const Ctx &c, int side, int line, int k)
-{
-    return (side ? c.s.KH : c.s.RH) + ((size_t)line * c.cw + (k >> 5)) * kHi;
-}
-
-// +1 / -1 on count[side][line][k] (one thread per line at a time).  Returns the
-// change in the number of counts >= 4, which selects the evaluation path, and
-// the updated shared word in *lo_out (may be null).
-__device__ __forceinline__ int count_step(const Ctx &c, int side, int line, int k, bool inc, uint4 *lo_out = nullptr)
-{
-    uint4 *w = lo_word(c, side, line, k);
-    uint4 a = *w;
+    const size_t w = plane_word(c, line, k);
+    uint2 a = c.s.P01[w];
+    uint32_t z = c.s.PH[w];
     const uint32_t bit = 1u << (k & 31);
-    const int old_hi = (a.z & bit) ? 1 : 0;
+    const int old_hi = (z & bit) ? 1 : 0;
     uint32_t carry = bit, t;
     t = inc ? (a.x & carry) : (~a.x & carry);
     a.x ^= carry;
@@ -249,7 +264,7 @@ __device__ __forceinline__ int count_step(const Ctx &c, int side, int line, int 
     a.y ^= carry;
     carry = t;
     if (carry) {                                   // crosses a multiple of 4: planes 2..6
-        uint32_t *g = hi_words(c, side, line, k);
+        uint32_t *g = c.s.HP + w * kHi;
         const uint4 g0 = *reinterpret_cast<const uint4 *>(g);
         uint32_t x[5] = {g0.x, g0.y, g0.z, g0.w, g[4]};
 #pragma unroll
@@ -260,54 +275,63 @@ __device__ __forceinline__ int count_step(const Ctx &c, int side, int line, int 
         }
         *reinterpret_cast<uint4 *>(g) = make_uint4(x[0], x[1], x[2], x[3]);
         g[4] = x[4];
-        a.z = ((x[0] | x[1] | x[2] | x[3] | x[4]) & bit) ? (a.z | bit) : (a.z & ~bit);
+        z = ((x[0] | x[1] | x[2] | x[3] | x[4]) & bit) ? (z | bit) : (z & ~bit);
+        c.s.PH[w] = z;
     }
-    *w = a;
-    if (lo_out) *lo_out = a;
-    return ((a.z & bit) ? 1 : 0) - old_hi;
+    c.s.P01[w] = a;
+    if (lo_out) *lo_out = make_uint4(a.x, a.y, z, 0u);
+    return ((z & bit) ? 1 : 0) - old_hi;
 }
 
-// count from a shared word: exact below 4, reported as 4 + (count mod 4) from 4 on,
-// which decides every "count > t" test with t <= 3 like the exact count
+// count from the shared words: exact below 4, reported as 4 + (count mod 4) from
+// 4 on, which decides every "count > t" test with t <= 3 like the exact count
 __device__ __forceinline__ int count_low(const uint4 &a, int k)
 {
     const uint32_t b = k & 31;
     return (int)(((a.x >> b) & 1u) | (((a.y >> b) & 1u) << 1) | (((a.z >> b) & 1u) << 2));
 }
 
-__device__ __forceinline__ int count_of_fast(const Ctx &c, int side, int line, int k)
+__device__ __forceinline__ int count_of_fast(const Ctx &c, int line, int k)
 {
-    return count_low(*lo_word(c, side, line, k), k);
+    const size_t w = plane_word(c, line, k);
+    const uint2 a = c.s.P01[w];
+    return count_low(make_uint4(a.x, a.y, c.s.PH[w], 0u), k);
 }
 
 // exact count (planes 2..6 read from global memory only when the count is >= 4)
-__device__ __forceinline__ int count_of(const Ctx &c, int side, int line, int k)
+__device__ __forceinline__ int count_of(const Ctx &c, int line, int k)
 {
-    const uint4 a = *lo_word(c, side, line, k);
+    const size_t w = plane_word(c, line, k);
+    const uint2 a = c.s.P01[w];
     const uint32_t b = k & 31;
     int x = (int)(((a.x >> b) & 1u) | (((a.y >> b) & 1u) << 1));
-    if ((a.z >> b) & 1u) {
-        const uint32_t *g = hi_words(c, side, line, k);
+    if ((c.s.PH[w] >> b) & 1u) {
+        const uint32_t *g = c.s.HP + w * kHi;
 #pragma unroll
         for (int p = 0; p < 5; ++p) x |= (int)((g[p] >> b) & 1u) << (p + 2);
     }
     return x;
 }
 
-__device__ __forceinline__ int gamma_of(const DevInst &I, const Ctx &c, int v, int k)
+__device__ __forceinline__ int gamma_of(const Ctx &c, int v, int k)
 {
     const uint16_t rc = c.rc[v];
-    return count_of(c, 0, rc >> 8, k) + count_of(c, 1, rc & 255, k) - 2;
+    return count_of(c, rc >> 8, k) + count_of(c, c.n + (rc & 255), k) - 2;
 }
 
-template <int NW>
-__device__ __forceinline__ void build_planes(const DevInst &I, const Ctx &c)
+// planes and member-id XOR tables from the colouring; returns the number of
+// counts >= 4 (also left in scal[2])
+template <int GT>
+__device__ __forceinline__ int build_planes(const DevInst &I, const Ctx &c)
 {
-    const int lo_words = 2 * I.n * c.cw * kLo, hi_words_n = 2 * I.n * c.cw * kHi;
-    for (int q = c.gt; q < lo_words; q += 32 * NW) c.s.RP[q] = 0u;   // RP and KP are contiguous
-    for (int q = c.gt; q < hi_words_n; q += 32 * NW) c.s.RH[q] = 0u;  // RH and KH are contiguous
-    gsync<NW>(c);
-    for (int l = c.gt; l < 2 * I.n; l += 32 * NW) {
+    const int words = 2 * I.n * c.cw, hi_words_n = 2 * I.n * c.cw * kHi;
+    for (int q = c.gt; q < words; q += GT) {
+        c.s.P01[q] = make_uint2(0u, 0u);
+        c.s.PH[q] = 0u;
+    }
+    for (int q = c.gt; q < hi_words_n; q += GT) c.s.HP[q] = 0u;
+    gsync<GT>(c);
+    for (int l = c.gt; l < 2 * I.n; l += GT) {
         const bool col = l >= I.n;
         const int line = col ? l - I.n : l;
         const int32_t *ptr = col ? I.col_ptr : I.row_ptr;
@@ -318,29 +342,31 @@ __device__ __forceinline__ void build_planes(const DevInst &I, const Ctx &c)
             const int u = __ldg(&lst[q]);
             const int k = c.s.S[u];
             if (k) {
-                count_step(c, col ? 1 : 0, line, k, true);
+                count_step(c, l, k, true);
                 X[k] ^= (uint16_t)u;
             }
         }
     }
-    gsync<NW>(c);
+    gsync<GT>(c);
     int hi = 0;
-    for (int t = c.gt; t < 2 * I.n * c.cw; t += 32 * NW) hi += __popc(c.s.RP[(size_t)t * kLo + 2]);
-    hi = gsum<NW>(hi, c);
+    for (int t = c.gt; t < words; t += GT) hi += __popc(c.s.PH[t]);
+    hi = gsum<GT>(hi, c);
     if (c.gt == 0) c.s.scal[2] = hi;
-    gsync<NW>(c);
+    gsync<GT>(c);
+    return hi;
 }
 
 // conflicting edges c(S) = sum over lines and colours of C(count, 2), from the
 // planes: sum of count^2 = sum_{p,q} 2^(p+q) popc(P_p & P_q)
-template <int NW>
+template <int GT>
 __device__ __forceinline__ int conflict_edges(const DevInst &I, const Ctx &c)
 {
     long long s = 0;
-    for (int t = c.gt; t < 2 * I.n * c.cw; t += 32 * NW) {
-        const uint32_t *lo = c.s.RP + (size_t)t * kLo, *g = c.s.RH + (size_t)t * kHi;
-        const bool high = lo[2] != 0u;
-        const uint32_t w[7] = {lo[0], lo[1], high ? g[0] : 0u, high ? g[1] : 0u, high ? g[2] : 0u,
+    for (int t = c.gt; t < 2 * I.n * c.cw; t += GT) {
+        const uint2 lo = c.s.P01[t];
+        const uint32_t *g = c.s.HP + (size_t)t * kHi;
+        const bool high = c.s.PH[t] != 0u;
+        const uint32_t w[7] = {lo.x, lo.y, high ? g[0] : 0u, high ? g[1] : 0u, high ? g[2] : 0u,
                                high ? g[3] : 0u, high ? g[4] : 0u};
         long long sq = 0, lin = 0;
 #pragma unroll
@@ -351,15 +377,15 @@ __device__ __forceinline__ int conflict_edges(const DevInst &I, const Ctx &c)
         }
         s += (sq - lin) / 2;
     }
-    return gsum<NW>((int)s, c);
+    return gsum<GT>((int)s, c);
 }
 
 // candidate bits (PLITS: V0 u C(S); PartialCol: V0), f and |C|; list = members
-template <int NW>
+template <int GT>
 __device__ __forceinline__ void build_cands(const DevInst &I, const Ctx &c, bool only_v0, int &f, int &nconf)
 {
     int lf = 0, lc = 0;
-    for (int wd = c.gt; wd < I.nw; wd += 32 * NW) {
+    for (int wd = c.gt; wd < I.nw; wd += GT) {
         uint32_t bits = 0;
         for (int b = 0; b < 32; ++b) {
             const int v = wd * 32 + b;
@@ -368,36 +394,38 @@ __device__ __forceinline__ void build_cands(const DevInst &I, const Ctx &c, bool
             if (k == 0) {
                 bits |= 1u << b;
                 ++lf;
-            } else if (gamma_of(I, c, v, k) > 0) {
+            } else if (gamma_of(c, v, k) > 0) {
                 ++lc;
                 if (!only_v0) bits |= 1u << b;
             }
         }
         c.s.cmask[wd] = bits;
     }
-    f = gsum<NW>(lf, c);
-    nconf = gsum<NW>(lc, c);
+    f = gsum<GT>(lf, c);
+    nconf = gsum<GT>(lc, c);
 }
 
-// rebuilds the candidate list from the bitmask (order is irrelevant)
-template <int NW>
-__device__ __forceinline__ void rebuild_list(const DevInst &I, const Ctx &c)
+// rebuilds the candidate list from the bitmask (order is irrelevant); returns
+// its length (also left in scal[0])
+template <int GT>
+__device__ __forceinline__ int rebuild_list(const DevInst &I, const Ctx &c)
 {
-    gsync<NW>(c);
+    constexpr int W = Grp<GT>::W, NW = Grp<GT>::NW;
+    gsync<GT>(c);
     const int w0 = (c.wg * I.nw) / NW, w1 = ((c.wg + 1) * I.nw) / NW;
     int cnt = 0;
-    for (int wd = w0 + c.lane; wd < w1; wd += 32) cnt += __popc(c.s.cmask[wd]);
+    for (int wd = w0 + c.gl; wd < w1; wd += W) cnt += __popc(c.s.cmask[wd]);
     int incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, o);
-        if (c.lane >= o) incl += y;
+    for (int o = 1; o < W; o <<= 1) {
+        const int y = __shfl_up_sync(c.gm, incl, o, W);
+        if (c.gl >= o) incl += y;
     }
-    const int wtotal = __shfl_sync(FULL, incl, 31);
+    const int wtotal = __shfl_sync(c.gm, incl, W - 1, W);
     int base = 0, total = wtotal;
     if (NW > 1) {
         if (c.lane == 0) c.s.scal[8 + c.wg] = wtotal;
-        gsync<NW>(c);
+        gsync<GT>(c);
         total = 0;
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
@@ -407,7 +435,7 @@ __device__ __forceinline__ void rebuild_list(const DevInst &I, const Ctx &c)
         }
     }
     int pos = base + incl - cnt;
-    for (int wd = w0 + c.lane; wd < w1; wd += 32) {
+    for (int wd = w0 + c.gl; wd < w1; wd += W) {
         uint32_t bits = c.s.cmask[wd];
         c.s.lmask[wd] = bits;
         while (bits) {
@@ -416,9 +444,10 @@ __device__ __forceinline__ void rebuild_list(const DevInst &I, const Ctx &c)
             c.s.list[pos++] = (uint16_t)(wd * 32 + b);
         }
     }
-    gsync<NW>(c);
+    gsync<GT>(c);
     if (c.gt == 0) c.s.scal[0] = total;
-    gsync<NW>(c);
+    gsync<GT>(c);
+    return total;
 }
 
 // ---- tabu cache -------------------------------------------------------------
@@ -427,16 +456,16 @@ struct Clock {
     uint32_t shift;   // relative clock = t - shift
 };
 
-template <int NW>
+template <int GT>
 __device__ __forceinline__ void tabu_reset(const DevInst &I, const Ctx &c)
 {
-    for (int v = c.gt; v < I.nv; v += 32 * NW) c.s.tc[v] = make_uint2(0u, 0xFFFFu);
+    for (int v = c.gt; v < I.nv; v += GT) c.s.tc[v] = make_uint2(0u, 0xFFFFu);
 }
 
-template <int NW>
+template <int GT>
 __device__ __forceinline__ void tabu_rebase(const DevInst &I, const Ctx &c)
 {
-    for (int v = c.gt; v < I.nv; v += 32 * NW) {
+    for (int v = c.gt; v < I.nv; v += GT) {
         const uint2 x = c.s.tc[v];
         uint32_t e0 = x.x & 0xFFFFu, e1 = x.x >> 16, em = x.y >> 16;
         e0 = e0 > kRebaseBy ? e0 - kRebaseBy : 0u;
@@ -632,12 +661,12 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
     const int i = c.s.S[v];
     const uint16_t rc = c.rc[v];
     const int r = rc >> 8, cc = rc & 255;
-    const uint32_t *RPr = line_planes(c.s.RP, NWC, r), *KPc = line_planes(c.s.KP, NWC, cc);
+    const uint2 *Pr = c.s.P01 + (size_t)r * NWC, *Pc = c.s.P01 + (size_t)(I.n + cc) * NWC;
     uint32_t s0[NWC], s1[NWC], s2[NWC];
 #pragma unroll
     for (int q = 0; q < NWC; ++q) {
-        const uint2 ra = *reinterpret_cast<const uint2 *>(RPr + q * kLo);
-        const uint2 ka = *reinterpret_cast<const uint2 *>(KPc + q * kLo);
+        const uint2 ra = Pr[q];
+        const uint2 ka = Pc[q];
         const uint32_t x0 = ra.x ^ ka.x, cy = ra.x & ka.x, x1 = ra.y ^ ka.y;
         s0[q] = x0;
         s1[q] = x1 ^ cy;
@@ -693,23 +722,22 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
 {
     const int i = c.s.S[v];
     const uint16_t rc = c.rc[v];
-    const int r = rc >> 8, cc = rc & 255;
-    const uint32_t *RPr = line_planes(c.s.RP, NWC, r), *KPc = line_planes(c.s.KP, NWC, cc);
+    const int r = rc >> 8, cc = rc & 255, rl = r, cl = I.n + cc;
     // s = R[r] + K[c] for every colour, bit-sliced
     uint32_t s[NWC][8];
 #pragma unroll
     for (int q = 0; q < NWC; ++q) {
-        const uint4 r0 = *reinterpret_cast<const uint4 *>(RPr + q * kLo);
-        const uint4 k0 = *reinterpret_cast<const uint4 *>(KPc + q * kLo);
+        const uint2 r0 = c.s.P01[(size_t)rl * NWC + q];
+        const uint2 k0 = c.s.P01[(size_t)cl * NWC + q];
         uint32_t a[7] = {r0.x, r0.y, 0u, 0u, 0u, 0u, 0u};
         uint32_t b[7] = {k0.x, k0.y, 0u, 0u, 0u, 0u, 0u};
-        if (r0.z) {
-            const uint32_t *g = c.s.RH + ((size_t)r * NWC + q) * kHi;
+        if (c.s.PH[(size_t)rl * NWC + q]) {
+            const uint32_t *g = c.s.HP + ((size_t)rl * NWC + q) * kHi;
 #pragma unroll
             for (int p = 0; p < 5; ++p) a[p + 2] = g[p];
         }
-        if (k0.z) {
-            const uint32_t *g = c.s.KH + ((size_t)cc * NWC + q) * kHi;
+        if (c.s.PH[(size_t)cl * NWC + q]) {
+            const uint32_t *g = c.s.HP + ((size_t)cl * NWC + q) * kHi;
 #pragma unroll
             for (int p = 0; p < 5; ++p) b[p + 2] = g[p];
         }
@@ -722,7 +750,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
         }
         s[q][7] = carry;
     }
-    const int gi = i ? count_of(c, 0, r, i) + count_of(c, 1, cc, i) - 2 : 0;
+    const int gi = i ? count_of(c, rl, i) + count_of(c, cl, i) - 2 : 0;
     const int base2 = i ? -mult * gi : base_unc;
     const int d2zero = 2 - mult * gi;
     const uint4 ar = c.allow[r], ac = c.allow[I.n + cc];
@@ -755,7 +783,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
                 }
             } else if (cs < 128u && test_bit<NWC>(m, cs)) {
                 clear_bit<NWC>(m, cs);
-                const int d2 = base2 + mult * (count_of(c, 0, r, (int)cs) + count_of(c, 1, cc, (int)cs));
+                const int d2 = base2 + mult * (count_of(c, rl, (int)cs) + count_of(c, cl, (int)cs));
                 if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
             }
         }
@@ -777,7 +805,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
             while (bits) {
                 const uint32_t j = q * 32 + __ffs(bits) - 1;
                 bits &= bits - 1;
-                const int d2 = base2 + mult * (count_of(c, 0, r, (int)j) + count_of(c, 1, cc, (int)j));
+                const int d2 = base2 + mult * (count_of(c, rl, (int)j) + count_of(c, cl, (int)j));
                 const bool tabu = (j == c0) ? (e0 >= trel) : (j == c1) ? (e1 >= trel) : (Gv[j] >= tabs);
                 if (!tabu || d2 < A) best = min(best, d2 * kKeyScale + (int)j);
             }
@@ -793,23 +821,23 @@ __device__ __forceinline__ int vertex_degree(const DevInst &I, const Ctx &c, int
 }
 
 // reserve a clock range for one phase of this slot
-template <int NW>
+template <int GT>
 __device__ __forceinline__ Clock claim_clock(const DevInst &I, const LSArgs &a, const Ctx &c, uint32_t *G, int slot, int span)
 {
-    gsync<NW>(c);
+    gsync<GT>(c);
     if (c.gt == 0) {
         uint32_t base = a.slot_clock[slot] + 1u;
         if (base > 0x7FFFFFFFu - (uint32_t)span) base = 0u;   // wrap: clear the slot
         c.s.scal[1] = (int)base;
     }
-    gsync<NW>(c);
+    gsync<GT>(c);
     uint32_t base = (uint32_t)c.s.scal[1];
     if (base == 0u) {
         const size_t words = (size_t)I.nv * I.n1p;
-        for (size_t q = c.gt; q < words; q += 32 * NW) G[q] = 0u;
+        for (size_t q = c.gt; q < words; q += GT) G[q] = 0u;
         base = 1u;
     }
-    gsync<NW>(c);
+    gsync<GT>(c);
     if (c.gt == 0) a.slot_clock[slot] = base + (uint32_t)span;
     Clock ck;
     ck.base = base;
@@ -828,15 +856,16 @@ __device__ __forceinline__ unsigned long long make_key(int kv, int v, int rsh, i
 }
 
 // group-wide minimum key and number of live candidates scanned
-template <int NW>
+template <int GT>
 __device__ __forceinline__ unsigned long long group_best(const Ctx &c, int parity, unsigned long long key,
                                                          int live, int &total)
 {
+    constexpr int NW = Grp<GT>::NW;
     const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
-    const uint32_t whi = __reduce_min_sync(FULL, hi);
-    const uint32_t wlo = __reduce_min_sync(FULL, hi == whi ? lo : 0xffffffffu);
+    const uint32_t whi = __reduce_min_sync(c.gm, hi);
+    const uint32_t wlo = __reduce_min_sync(c.gm, hi == whi ? lo : 0xffffffffu);
     const unsigned long long wk = ((unsigned long long)whi << 32) | wlo;
-    const int wl = __reduce_add_sync(FULL, live);
+    const int wl = __reduce_add_sync(c.gm, live);
     if (NW == 1) {
         total = wl;
         return wk;
@@ -845,7 +874,7 @@ __device__ __forceinline__ unsigned long long group_best(const Ctx &c, int parit
         c.s.red[parity * NW + c.wg] = wk;
         c.s.red_cnt[parity * NW + c.wg] = wl;
     }
-    gsync<NW>(c);
+    gsync<GT>(c);
     unsigned long long best = kNoKey;
     total = 0;
 #pragma unroll
@@ -856,10 +885,10 @@ __device__ __forceinline__ unsigned long long group_best(const Ctx &c, int parit
     return best;
 }
 
-// warp 0 of the group: appends the lanes' flagged vertices to the candidate list
+// first warp of the group: appends the lanes' flagged vertices to the candidate list
 __device__ __forceinline__ void list_append(const Ctx &c, bool want, int u, int &len)
 {
-    const uint32_t b = __ballot_sync(FULL, want);
+    const uint32_t b = __ballot_sync(c.gm, want);
     if (want) {
         const int pos = len + __popc(b & ((1u << c.lane) - 1u));
         c.s.list[pos] = (uint16_t)u;
@@ -868,14 +897,15 @@ __device__ __forceinline__ void list_append(const Ctx &c, bool want, int u, int 
     len += __popc(b);
 }
 
-// One scan pass of a one-warp walk over list entries base .. base+31: stale
-// entries (no longer candidates) are dropped and lose their membership bit, live
-// ones are written back contiguously at wpos, so the list stays about as long as
-// the candidate set and a scan needs no pass over stale entries.  Returns the
-// lane's live vertex or -1.
+// One scan pass of a single-warp group over list entries base .. base+W-1:
+// stale entries (no longer candidates) are dropped and lose their membership
+// bit, live ones are written back contiguously at wpos, so the list stays about
+// as long as the candidate set and a scan needs no pass over stale entries.
+// Returns the lane's live vertex or -1.
+template <int W>
 __device__ __forceinline__ int list_pass(const Ctx &c, int base, int len, int &wpos)
 {
-    const int qq = base + c.lane;
+    const int qq = base + c.gl;
     int v = -1;
     bool lv = false;
     if (qq < len) {
@@ -883,8 +913,8 @@ __device__ __forceinline__ int list_pass(const Ctx &c, int base, int len, int &w
         lv = (c.s.cmask[v >> 5] >> (v & 31)) & 1u;
         if (!lv) atomicAnd(&c.s.lmask[v >> 5], ~(1u << (v & 31)));
     }
-    const uint32_t b = __ballot_sync(FULL, lv);
-    __syncwarp();                                     // every entry of the pass read before any write
+    const uint32_t b = __ballot_sync(c.gm, lv);
+    __syncwarp(c.gm);                                 // every entry of the pass read before any write
     const int to = wpos + __popc(b & ((1u << c.lane) - 1u));
     if (lv && to != qq) c.s.list[to] = (uint16_t)v;  // entries that do not move stay cached
     wpos += __popc(b);
@@ -892,21 +922,25 @@ __device__ __forceinline__ int list_pass(const Ctx &c, int base, int len, int &w
 }
 
 // ---- PLITS phase (Alg. 3 with phi2 = 2*phi) --------------------------------
-template <int NWC, int NW>
+// Within one warp (GT <= 32) the list length, |C(S)|, the number of counts >= 4
+// and the check result are known to every lane after the move's collectives
+// and stay in registers; wider groups pass them through the slot's scalars.
+template <int NWC, int GT>
 __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, const Ctx &c, uint32_t *G, uint8_t *gbest,
                             int slot, int ind, int phase, int64_t N, int phi2, int span, LaneStats &st,
                             long long &F2best_out)
 {
-    build_planes<NW>(I, c);
+    constexpr int W = Grp<GT>::W, NW = Grp<GT>::NW;
+    int hi = build_planes<GT>(I, c);
     int f, nconf;
-    build_cands<NW>(I, c, false, f, nconf);
-    const int cedges = conflict_edges<NW>(I, c);
+    build_cands<GT>(I, c, false, f, nconf);
+    const int cedges = conflict_edges<GT>(I, c);
     long long F2 = 2LL * f + (long long)phi2 * cedges;
     long long F2best = F2;
-    gcopy<NW>(gbest, c.s.S, I.nv, c);
-    tabu_reset<NW>(I, c);
-    rebuild_list<NW>(I, c);
-    Clock ck = claim_clock<NW>(I, a, c, G, slot, span);
+    gcopy<GT>(gbest, c.s.S, I.nv, c);
+    tabu_reset<GT>(I, c);
+    int len = rebuild_list<GT>(I, c);
+    Clock ck = claim_clock<GT>(I, a, c, G, slot, span);
 
     const uint32_t ctr2 = ((uint32_t)a.gen << 8) | (kPurposeTabu << 4) | (uint32_t)phase;
     uint32_t Lr = 0, rotr = 0;
@@ -915,29 +949,29 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         if (f + nconf == 0) break;                       // nothing left to improve
         uint32_t trel = (uint32_t)(t - ck.shift);
         if (trel >= kRebaseAt) {
-            gsync<NW>(c);
-            tabu_rebase<NW>(I, c);
+            gsync<GT>(c);
+            tabu_rebase<GT>(I, c);
             ck.shift += kRebaseBy;
             trel -= kRebaseBy;
-            gsync<NW>(c);
+            gsync<GT>(c);
         }
-        int len = c.s.scal[0];
-        if (len > 2 * (f + nconf) + 64) {
-            rebuild_list<NW>(I, c);
+        if (NW > 1) {
             len = c.s.scal[0];
+            hi = c.s.scal[2];
         }
-        const int q = (int)((t - 1) & 31);
+        if (len > 2 * (f + nconf) + 64) len = rebuild_list<GT>(I, c);
+        const int q = (int)((t - 1) & (W - 1));
         if (q == 0) {
-            const uint4 u = philox4x32_10(make_uint4((uint32_t)(t + c.lane), (uint32_t)ind, ctr2, 0u), a.key0, a.key1);
+            const uint4 u = philox4x32_10(make_uint4((uint32_t)(t + c.gl), (uint32_t)ind, ctr2, 0u), a.key0, a.key1);
             Lr = bounded(u.x, (uint32_t)a.tenure_rand);
             rotr = bounded(u.y, (uint32_t)I.nv);
         }
-        const int L = (int)__shfl_sync(FULL, Lr, q);
-        const int rsh = (int)__shfl_sync(FULL, rotr, q);
+        const int L = (int)__shfl_sync(c.gm, Lr, q, W);
+        const int rsh = (int)__shfl_sync(c.gm, rotr, q, W);
         const long long A64 = F2best - F2;
         const int A = A64 < -(1LL << 30) ? -(1 << 30) : (int)A64;
 
-        const bool low = c.s.scal[2] == 0;            // every count <= 3
+        const bool low = hi == 0;                     // every count <= 3
         unsigned long long key = kNoKey;
         int live = 0;
         auto consider = [&](int v) {
@@ -952,21 +986,19 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         };
         if constexpr (NW == 1) {
             int wpos = 0;
-            for (int base = 0; base < len; base += 32) {
-                const int v = list_pass(c, base, len, wpos);
+            for (int base = 0; base < len; base += W) {
+                const int v = list_pass<W>(c, base, len, wpos);
                 if (v >= 0) consider(v);
             }
-            if (c.lane == 0) c.s.scal[0] = wpos;
-            __syncwarp();
             len = wpos;
         } else {
-            for (int qq = c.gt; qq < len; qq += 32 * NW) {
+            for (int qq = c.gt; qq < len; qq += GT) {
                 const int v = c.s.list[qq];
                 if ((c.s.cmask[v >> 5] >> (v & 31)) & 1u) consider(v);   // else a stale entry
             }
         }
         int ncand;
-        const unsigned long long best = group_best<NW>(c, (int)(t & 1), key, live, ncand);
+        const unsigned long long best = group_best<GT>(c, (int)(t & 1), key, live, ncand);
         if (ncand != f + nconf) { ok = false; break; }
         st.iterations += 1;
         st.cand += ncand;
@@ -979,6 +1011,7 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         if (v >= I.nv) v -= I.nv;
         f += (j == 0) - (i == 0);
         F2 += d2;
+        bool bad = false;
         if (c.wg == 0) {
             const uint16_t rc = c.rc[v];
             const int r = rc >> 8, cc = rc & 255;
@@ -989,51 +1022,49 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             // member-id XOR of (row r | column cc, colour i | j), read first so that
             // its latency overlaps the count updates: lane 0 row/i, 1 column/i,
             // 2 row/j, 3 column/j
-            const int xk = c.lane < 2 ? i : j;
-            const size_t xidx = (size_t)((c.lane & 1) ? I.n + cc : r) * I.n1p + xk;
-            const int xold = (c.lane < 4 && xk) ? (int)c.s.xr[xidx] : 0;
-            int cnt_i = 0, cnt_j = 0;
-            if (c.lane < 4) {
-                const int side = c.lane & 1;
-                const int line = side ? cc : r;
-                int dh = 0;
+            const int xk = c.gl < 2 ? i : j;
+            const int xline = (c.gl & 1) ? I.n + cc : r;
+            const size_t xidx = (size_t)xline * I.n1p + xk;
+            const int xold = (c.gl < 4 && xk) ? (int)c.s.xr[xidx] : 0;
+            int cnt_i = 0, cnt_j = 0, dh = 0;
+            if (c.gl < 4) {
                 uint4 w;
-                if (c.lane < 2) {
-                    if (i) dh += count_step(c, side, line, i, false, &w);
-                    if (same) dh += count_step(c, side, line, j, true, &w);
+                if (c.gl < 2) {
+                    if (i) dh += count_step(c, xline, i, false, &w);
+                    if (same) dh += count_step(c, xline, j, true, &w);
                     if (i) cnt_i = count_low(w, i);       // counts after the move (4 = four or more)
                     if (same) cnt_j = count_low(w, j);
                 } else if (j && !same) {
-                    dh += count_step(c, side, line, j, true, &w);
+                    dh += count_step(c, xline, j, true, &w);
                     cnt_j = count_low(w, j);
                 }
-                if (dh) atomicAdd(&c.s.scal[2], dh);
-                if (c.lane == 0) c.s.S[v] = (uint8_t)j;
+                if (c.gl == 0) c.s.S[v] = (uint8_t)j;
                 if (xk) c.s.xr[xidx] = (uint16_t)(xold ^ v);   // v leaves i, joins j
             }
+            const int dh_tot = __reduce_add_sync(c.gm, dh);
             // counts of colours i and j on the moved row and column, after the move
-            const int Ri = __shfl_sync(FULL, cnt_i, 0), Ki = __shfl_sync(FULL, cnt_i, 1);
-            const int Rj = __shfl_sync(FULL, cnt_j, same ? 0 : 2), Kj = __shfl_sync(FULL, cnt_j, same ? 1 : 3);
-            __syncwarp();
+            const int Ri = __shfl_sync(c.gm, cnt_i, 0, W), Ki = __shfl_sync(c.gm, cnt_i, 1, W);
+            const int Rj = __shfl_sync(c.gm, cnt_j, same ? 0 : 2, W), Kj = __shfl_sync(c.gm, cnt_j, same ? 1 : 3, W);
+            __syncwarp(c.gm);
             // The mates whose conflict status can change, one per (line, colour) at
             // most: the only other holder of colour i (count after the move 1) and
             // the other holder of colour j (count after 2).  Each is read from the
             // member-id XOR of its line: lane 0 row/i, 1 column/i, 2 row/j, 3 column/j.
             int dconf = 0;
             int u = -1, su = 0, cl = 0;
-            const bool row_mate = (c.lane & 1) == 0;
-            if (c.lane == 0 && i && Ri == 1) { u = xold ^ v; su = i; cl = Ri; }   // the last holder of i
-            if (c.lane == 1 && i && Ki == 1) { u = xold ^ v; su = i; cl = Ki; }
-            if (c.lane == 2 && j && Rj == 2) { u = xold; su = j; cl = Rj; }       // the other holder of j
-            if (c.lane == 3 && j && Kj == 2) { u = xold; su = j; cl = Kj; }
+            const bool row_mate = (c.gl & 1) == 0;
+            if (c.gl == 0 && i && Ri == 1) { u = xold ^ v; su = i; cl = Ri; }   // the last holder of i
+            if (c.gl == 1 && i && Ki == 1) { u = xold ^ v; su = i; cl = Ki; }
+            if (c.gl == 2 && j && Rj == 2) { u = xold; su = j; cl = Rj; }       // the other holder of j
+            if (c.gl == 3 && j && Kj == 2) { u = xold; su = j; cl = Kj; }
             bool want = false, bad_mate = false;
             if (u >= 0) {
                 if (u >= I.nv || u == v || c.s.S[u] != su) {
                     bad_mate = true;                     // inconsistent table: report, touch nothing
                 } else {
                     const uint16_t urc = c.rc[u];
-                    const int g = cl + (row_mate ? count_of_fast(c, 1, urc & 255, su)
-                                                 : count_of_fast(c, 0, urc >> 8, su)) - 2;
+                    const int g = cl + (row_mate ? count_of_fast(c, I.n + (urc & 255), su)
+                                                 : count_of_fast(c, urc >> 8, su)) - 2;
                     const int nc = g > 0, oc = (c.s.cmask[u >> 5] >> (u & 31)) & 1;
                     if (nc != oc) {
                         atomicXor(&c.s.cmask[u >> 5], 1u << (u & 31));
@@ -1043,81 +1074,91 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
                 }
             }
             list_append(c, want, u, len);
-            const bool any_bad = __any_sync(FULL, bad_mate);
-            if (c.lane == 0) {
+            bad = __any_sync(c.gm, bad_mate);
+            if (c.gl == 0) {
                 const int newc = j ? (int)(Rj + Kj - 2 > 0) : 0;
                 if (j != 0 && !newc) atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
                 dconf += newc - (i != 0 ? 1 : 0);
             }
-            dconf = __reduce_add_sync(FULL, dconf);
-            if (c.lane == 0) {
+            dconf = __reduce_add_sync(c.gm, dconf);
+            if (c.gl == 0) {
                 const int k = f + nconf + dconf;
                 const int T = L + tenure_div(a, a.alpha_num * k);
                 tabu_insert(I, c, G, ck, v, i, trel + (uint32_t)T);
+            }
+            if (NW == 1) {
+                nconf += dconf;
+                hi += dh_tot;
+            } else if (c.lane == 0) {
                 c.s.scal[4] = nconf + dconf;
                 c.s.scal[0] = len;
-                c.s.scal[6] = any_bad ? 1 : 0;
+                c.s.scal[2] = hi + dh_tot;
+                c.s.scal[6] = bad ? 1 : 0;
             }
         }
-        gsync<NW>(c);
-        if (c.s.scal[6]) { ok = false; break; }
-        nconf = c.s.scal[4];
+        gsync<GT>(c);
+        if (NW > 1) {
+            bad = c.s.scal[6] != 0;
+            nconf = c.s.scal[4];
+        }
+        if (bad) { ok = false; break; }
         st.moves += 1;
         if (c.gt == 0) st.deg += vertex_degree(I, c, v);
         if (F2 < F2best) {
             F2best = F2;
             st.improvements += 1;
-            gcopy<NW>(gbest, c.s.S, I.nv, c);
+            gcopy<GT>(gbest, c.s.S, I.nv, c);
         }
     }
-    gsync<NW>(c);
-    gcopy<NW>(c.s.S, gbest, I.nv, c);
-    gsync<NW>(c);
+    gsync<GT>(c);
+    gcopy<GT>(c.s.S, gbest, I.nv, c);
+    gsync<GT>(c);
     F2best_out = F2best;
     return ok;
 }
 
 // ---- greedy conflict removal (Sec. 3.7) ------------------------------------
-template <int NW>
+template <int GT>
 __device__ __forceinline__ void repair(const DevInst &I, const Ctx &c)
 {
-    build_planes<NW>(I, c);
+    build_planes<GT>(I, c);
     for (int step = 0; step < I.nv; ++step) {
         uint32_t key = 0;
-        for (int v = c.gt; v < I.nv; v += 32 * NW) {
+        for (int v = c.gt; v < I.nv; v += GT) {
             const int k = c.s.S[v];
             if (!k) continue;
-            const int g = gamma_of(I, c, v, k);
+            const int g = gamma_of(c, v, k);
             if (g > 0) key = max(key, ((uint32_t)g << 16) | (0xFFFFu - (uint32_t)v));
         }
-        const uint32_t m = gmax<NW>(key, c);
+        const uint32_t m = gmax<GT>(key, c);
         if (m == 0u) break;
         const int v = (int)(0xFFFFu - (m & 0xFFFFu));
-        gsync<NW>(c);
+        gsync<GT>(c);
         if (c.gt == 0) {
             const int k = c.s.S[v];
             const uint16_t rc = c.rc[v];
             c.s.S[v] = 0;
-            c.s.scal[2] += count_step(c, 0, rc >> 8, k, false) + count_step(c, 1, rc & 255, k, false);
+            c.s.scal[2] += count_step(c, rc >> 8, k, false) + count_step(c, I.n + (rc & 255), k, false);
         }
-        gsync<NW>(c);
+        gsync<GT>(c);
     }
 }
 
 // ---- PartialCol (Sec. 3.7): legal partial colourings only ------------------
-template <int NWC, int NW>
+template <int NWC, int GT>
 __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs &a, const Ctx &c, uint32_t *G, uint8_t *gbest,
                                  int slot, int ind, int64_t N, int span, LaneStats &st, long long &fbest_out)
 {
-    build_planes<NW>(I, c);
+    constexpr int W = Grp<GT>::W, NW = Grp<GT>::NW;
+    build_planes<GT>(I, c);
     int f, nconf;
-    build_cands<NW>(I, c, true, f, nconf);
-    if (conflict_edges<NW>(I, c) != 0) return false;    // needs a legal start
+    build_cands<GT>(I, c, true, f, nconf);
+    if (conflict_edges<GT>(I, c) != 0) return false;    // needs a legal start
     int fbest = f;
-    gcopy<NW>(gbest, c.s.S, I.nv, c);
-    tabu_reset<NW>(I, c);
-    rebuild_list<NW>(I, c);
-    Clock ck = claim_clock<NW>(I, a, c, G, slot, span);
+    gcopy<GT>(gbest, c.s.S, I.nv, c);
+    tabu_reset<GT>(I, c);
+    rebuild_list<GT>(I, c);
+    Clock ck = claim_clock<GT>(I, a, c, G, slot, span);
     const uint32_t ctr2 = ((uint32_t)a.gen << 8) | (kPurposeTabu << 4) | 3u;
     uint32_t Lr = 0, rotr = 0;
     bool ok = true;
@@ -1126,25 +1167,22 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         if (f == 0) break;
         uint32_t trel = (uint32_t)(t - ck.shift);
         if (trel >= kRebaseAt) {
-            gsync<NW>(c);
-            tabu_rebase<NW>(I, c);
+            gsync<GT>(c);
+            tabu_rebase<GT>(I, c);
             ck.shift += kRebaseBy;
             trel -= kRebaseBy;
-            gsync<NW>(c);
+            gsync<GT>(c);
         }
         int len = c.s.scal[0];
-        if (len > 2 * f + 64) {
-            rebuild_list<NW>(I, c);
-            len = c.s.scal[0];
-        }
-        const int q = (int)((t - 1) & 31);
+        if (len > 2 * f + 64) len = rebuild_list<GT>(I, c);
+        const int q = (int)((t - 1) & (W - 1));
         if (q == 0) {
-            const uint4 u = philox4x32_10(make_uint4((uint32_t)(t + c.lane), (uint32_t)ind, ctr2, 0u), a.key0, a.key1);
+            const uint4 u = philox4x32_10(make_uint4((uint32_t)(t + c.gl), (uint32_t)ind, ctr2, 0u), a.key0, a.key1);
             Lr = bounded(u.x, (uint32_t)a.tenure_rand);
             rotr = bounded(u.y, (uint32_t)I.nv);
         }
-        const int L = (int)__shfl_sync(FULL, Lr, q);
-        const int rsh = (int)__shfl_sync(FULL, rotr, q);
+        const int L = (int)__shfl_sync(c.gm, Lr, q, W);
+        const int rsh = (int)__shfl_sync(c.gm, rotr, q, W);
         const int A = fbest - f;
         const bool low = c.s.scal[2] == 0;            // every count <= 3
         unsigned long long key = kNoKey;
@@ -1161,21 +1199,21 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         };
         if constexpr (NW == 1) {
             int wpos = 0;
-            for (int base = 0; base < len; base += 32) {
-                const int v = list_pass(c, base, len, wpos);
+            for (int base = 0; base < len; base += W) {
+                const int v = list_pass<W>(c, base, len, wpos);
                 if (v >= 0) consider(v);
             }
-            if (c.lane == 0) c.s.scal[0] = wpos;
-            __syncwarp();
+            if (c.gl == 0) c.s.scal[0] = wpos;
+            __syncwarp(c.gm);
             len = wpos;
         } else {
-            for (int qq = c.gt; qq < len; qq += 32 * NW) {
+            for (int qq = c.gt; qq < len; qq += GT) {
                 const int v = c.s.list[qq];
                 if ((c.s.cmask[v >> 5] >> (v & 31)) & 1u) consider(v);
             }
         }
         int ncand;
-        const unsigned long long best = group_best<NW>(c, (int)(t & 1), key, live, ncand);
+        const unsigned long long best = group_best<GT>(c, (int)(t & 1), key, live, ncand);
         if (ncand != f) { ok = false; break; }
         st.iterations += 1;
         st.cand += ncand;
@@ -1190,55 +1228,55 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
             const uint16_t rc = c.rc[v];
             const int r = rc >> 8, cc = rc & 255;
             const int T = L + tenure_div(a, a.alpha_num * (f + d));
-            if (c.lane == 0) c.s.scal[5] = 0;
-            __syncwarp();
+            if (c.gl == 0) c.s.scal[5] = 0;
+            __syncwarp(c.gm);
             // row- and column-mates coloured j lose their colour
             for (int side = 0; side < 2; ++side) {
                 const int32_t *ptr = side ? I.col_ptr : I.row_ptr;
                 const uint16_t *lst = side ? I.col_v : I.row_v;
                 const int line = side ? cc : r;
                 const int qb = __ldg(&ptr[line]), qe = __ldg(&ptr[line + 1]);
-                for (int qq = qb + c.lane; qq < qe; qq += 32) {
+                for (int qq = qb + c.gl; qq < qe; qq += W) {
                     const int u = __ldg(&lst[qq]);
                     if (u == v || c.s.S[u] != j) continue;
                     const int k = atomicAdd(&c.s.scal[5], 1);
                     if (k < 8) ulist[k] = u;
                 }
             }
-            __syncwarp();
+            __syncwarp(c.gm);
             const int nunc = c.s.scal[5];
             const bool bad = nunc > 8 || nunc - 1 != d;
             int wantu = 0;
             bool want = false;
-            if (!bad && c.lane < nunc) {
-                wantu = ulist[c.lane];
+            if (!bad && c.gl < nunc) {
+                wantu = ulist[c.gl];
                 want = !((c.s.lmask[wantu >> 5] >> (wantu & 31)) & 1u);
             }
-            __syncwarp();
+            __syncwarp(c.gm);
             if (!bad) {
-                if (c.lane == 0) {
+                if (c.gl == 0) {
                     for (int k = 0; k < nunc; ++k) {
                         const int u = ulist[k];
                         const uint16_t rcu = c.rc[u];
                         c.s.S[u] = 0;
-                        c.s.scal[2] += count_step(c, 0, rcu >> 8, j, false) +
-                                       count_step(c, 1, rcu & 255, j, false);
+                        c.s.scal[2] += count_step(c, rcu >> 8, j, false) +
+                                       count_step(c, I.n + (rcu & 255), j, false);
                         atomicOr(&c.s.cmask[u >> 5], 1u << (u & 31));
                         tabu_insert(I, c, G, ck, u, j, trel + (uint32_t)T);
                     }
                     c.s.S[v] = (uint8_t)j;
-                    c.s.scal[2] += count_step(c, 0, r, j, true) + count_step(c, 1, cc, j, true);
+                    c.s.scal[2] += count_step(c, r, j, true) + count_step(c, I.n + cc, j, true);
                     atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
                 }
-                __syncwarp();
+                __syncwarp(c.gm);
                 list_append(c, want, wantu, len);
             }
-            if (c.lane == 0) {
+            if (c.gl == 0) {
                 c.s.scal[6] = bad ? 1 : 0;
                 c.s.scal[0] = len;
             }
         }
-        gsync<NW>(c);
+        gsync<GT>(c);
         if (c.s.scal[6]) { ok = false; break; }
         if (c.gt == 0) st.uncolored += c.s.scal[5];
         f += d;
@@ -1247,22 +1285,19 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         if (f < fbest) {
             fbest = f;
             st.improvements += 1;
-            gcopy<NW>(gbest, c.s.S, I.nv, c);
+            gcopy<GT>(gbest, c.s.S, I.nv, c);
         }
     }
-    gsync<NW>(c);
-    gcopy<NW>(c.s.S, gbest, I.nv, c);
-    gsync<NW>(c);
+    gsync<GT>(c);
+    gcopy<GT>(c.s.S, gbest, I.nv, c);
+    gsync<GT>(c);
     fbest_out = fbest;
     return ok;
 }
 
-template <int NWC, int NW>
-__global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_search_kernel(const DevInst I, const LSArgs a, int walks)
+// instance data shared by every walk slot of the block
+__device__ __forceinline__ void load_instance(const DevInst &I, uint8_t *smem)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
-    if (a.skip && *a.skip) return;
-    // instance data shared by every walk slot of the block
     uint16_t *rc_s = reinterpret_cast<uint16_t *>(smem);
     uint4 *allow_s = reinterpret_cast<uint4 *>(smem + align16(2 * (size_t)I.nv));
     for (int v = threadIdx.x; v < I.nv; v += blockDim.x) rc_s[v] = __ldg(&I.rc[v]);
@@ -1271,50 +1306,55 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
         allow_s[r] = r < I.n ? I.allow_row[r] : I.allow_col[r - I.n];
         len_s[r] = (uint8_t)(r < I.n ? I.row_ptr[r + 1] - I.row_ptr[r] : I.col_ptr[r - I.n + 1] - I.col_ptr[r - I.n]);
     }
-    __syncthreads();
+}
 
-    Ctx c = make_ctx<NW>(smem, I);
+// The walk groups of one block take walks of one launch (instance I, arguments
+// a) from its counter until none is left.
+template <int NWC, int GT>
+__device__ __forceinline__ void walk_loop(const DevInst &I, const LSArgs &a, int walks, uint8_t *smem)
+{
+    Ctx c = make_ctx<GT>(smem, I, a.s_smem != 0);
     if (c.g >= walks) return;
     const int slot = blockIdx.x * walks + c.g;
     uint32_t *G = a.G + (size_t)slot * I.nv * I.n1p;
     c.s.tc = a.TC + (size_t)slot * I.nv;
     c.s.list = a.LIST + (size_t)slot * I.nv;
     c.s.xr = a.XR + (size_t)slot * 2 * I.n * I.n1p;
-    c.s.RH = a.HP + (size_t)slot * 2 * I.n * c.cw * kHi;
-    c.s.KH = c.s.RH + (size_t)I.n * c.cw * kHi;
+    c.s.HP = a.HP + (size_t)slot * 2 * I.n * c.cw * kHi;
+    if (!a.s_smem) c.s.S = a.SW + (size_t)slot * align16((size_t)I.nv);
 
     for (;;) {
         if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);
-        gsync<NW>(c);
+        gsync<GT>(c);
         const int wk = c.s.scal[7];
-        gsync<NW>(c);
+        gsync<GT>(c);
         if (wk >= a.count) break;
         const int ind = a.ind0 + wk;
         const uint8_t *gin = a.S_in + (size_t)wk * I.nv;
         uint8_t *gout = a.S_out + (size_t)wk * I.nv;
-        gcopy<NW>(c.s.S, gin, I.nv, c);
-        gsync<NW>(c);
+        gcopy<GT>(c.s.S, gin, I.nv, c);
+        gsync<GT>(c);
 
         LaneStats st = {0, 0, 0, 0, 0, 0, 0};
         long long Flast = 0;
         bool ok = true;
         if (a.flags & PLSE_LS_PARTIALCOL) {
-            if (a.flags & PLSE_LS_REPAIR) repair<NW>(I, c);
-            ok = partialcol_phase<NWC, NW>(I, a, c, G, gout, slot, ind, a.iters1, a.span1, st, Flast);
+            if (a.flags & PLSE_LS_REPAIR) repair<GT>(I, c);
+            ok = partialcol_phase<NWC, GT>(I, a, c, G, gout, slot, ind, a.iters1, a.span1, st, Flast);
         } else {
             if (a.flags & PLSE_LS_PHASE1)
-                ok = plits_phase<NWC, NW>(I, a, c, G, gout, slot, ind, 1, a.iters1, a.phi2_1, a.span1, st, Flast);
+                ok = plits_phase<NWC, GT>(I, a, c, G, gout, slot, ind, 1, a.iters1, a.phi2_1, a.span1, st, Flast);
             if (ok && (a.flags & PLSE_LS_PHASE2))
-                ok = plits_phase<NWC, NW>(I, a, c, G, gout, slot, ind, 2, a.iters2, a.phi2_2, a.span2, st, Flast);
-            if (ok && (a.flags & PLSE_LS_REPAIR)) repair<NW>(I, c);
+                ok = plits_phase<NWC, GT>(I, a, c, G, gout, slot, ind, 2, a.iters2, a.phi2_2, a.span2, st, Flast);
+            if (ok && (a.flags & PLSE_LS_REPAIR)) repair<GT>(I, c);
         }
-        gsync<NW>(c);
+        gsync<GT>(c);
         if (!ok && c.gt == 0) atomicOr(a.error_flag, 1);
-        gcopy<NW>(gout, c.s.S, I.nv, c);
+        gcopy<GT>(gout, c.s.S, I.nv, c);
         int z = 0;
-        for (int q = c.gt; q < I.nv; q += 32 * NW) z += (c.s.S[q] == 0);
-        const int fz = gsum<NW>(z, c);
-        const long long pairs = gsum64<NW>(st.pairs, c);
+        for (int q = c.gt; q < I.nv; q += GT) z += (c.s.S[q] == 0);
+        const int fz = gsum<GT>(z, c);
+        const long long pairs = gsum64<GT>(st.pairs, c);
         if (c.gt == 0) {
             if (a.f_out) a.f_out[wk] = fz;
             if (a.F_out) a.F_out[wk] = Flast;
@@ -1330,7 +1370,47 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
                 a.stats[wk] = s;
             }
         }
-        gsync<NW>(c);
+        gsync<GT>(c);
+    }
+}
+
+template <int NWC, int GT>
+__global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_search_kernel(const DevInst I, const LSArgs a, int walks)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    if (a.skip && *a.skip) return;
+    load_instance(I, smem);
+    __syncthreads();
+    walk_loop<NWC, GT>(I, a, walks, smem);
+}
+
+// Several launches' worth of walks (one per job, e.g. the same generation of
+// several runs) in one persistent launch: every block takes the jobs in order,
+// loads a job's instance part when it starts on it and moves to the next job
+// as soon as the job's counter runs out, so blocks that finish early fill the
+// tail of one job with walks of the next.  The job descriptors are copied to
+// shared memory; the slots of the block use the job's own layout.
+template <int NWC, int GT>
+__global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2)
+local_search_multi_kernel(const LSJob *jobs, int njobs, int walks, int s_smem)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ DevInst sI;
+    __shared__ LSArgs sA;
+    __shared__ int sskip;
+    for (int j = 0; j < njobs; ++j) {
+        __syncthreads();                           // the previous job's slots are no longer in use
+        if (threadIdx.x == 0) {
+            sI = jobs[j].I;
+            sA = jobs[j].a;
+            sA.s_smem = s_smem;
+            sskip = sA.skip ? *sA.skip : 0;
+        }
+        __syncthreads();
+        if (sskip) continue;
+        load_instance(sI, smem);
+        __syncthreads();
+        walk_loop<NWC, GT>(sI, sA, walks, smem);
     }
 }
 
@@ -1365,83 +1445,133 @@ __global__ void init_population_kernel(const DevInst I, int pop, uint32_t k0, ui
     }
 }
 
-template <int NWC, int NW>
+template <int NWC, int GT>
 cudaError_t launch_t(const DevInst &I, const LSArgs &a, const LSLaunch &L, cudaStream_t st)
 {
-    local_search_kernel<NWC, NW><<<L.blocks, 32 * NW * L.walks, L.smem, st>>>(I, a, L.walks);
+    local_search_kernel<NWC, GT><<<L.blocks, GT * L.walks, L.smem, st>>>(I, a, L.walks);
     return cudaGetLastError();
 }
 
 template <int NWC>
-cudaError_t launch_w(const DevInst &I, const LSArgs &a, const LSLaunch &L, cudaStream_t st)
+cudaError_t launch_g(const DevInst &I, const LSArgs &a, const LSLaunch &L, cudaStream_t st)
 {
-    switch (L.warps) {
-        case 1: return launch_t<NWC, 1>(I, a, L, st);
-        case 2: return launch_t<NWC, 2>(I, a, L, st);
-        case 4: return launch_t<NWC, 4>(I, a, L, st);
-        default: return launch_t<NWC, 8>(I, a, L, st);
+    switch (L.group) {
+        case 16: return launch_t<NWC, 16>(I, a, L, st);
+        case 32: return launch_t<NWC, 32>(I, a, L, st);
+        case 64: return launch_t<NWC, 64>(I, a, L, st);
+        case 128: return launch_t<NWC, 128>(I, a, L, st);
+        default: return launch_t<NWC, 256>(I, a, L, st);
     }
 }
 
 // sets the block's shared-memory size; returns resident blocks per SM
-template <int NWC, int NW>
+template <int NWC, int GT>
 int set_smem_t(size_t smem, int threads)
 {
-    cudaFuncSetAttribute(local_search_kernel<NWC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(local_search_kernel<NWC, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, local_search_kernel<NWC, NW>, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, local_search_kernel<NWC, GT>, threads, smem) !=
         cudaSuccess)
         per_sm = 0;
     return per_sm;
 }
 
 template <int NWC>
-int set_smem_w(int warps, size_t smem, int threads)
+int set_smem_g(int group, size_t smem, int threads)
 {
-    switch (warps) {
-        case 1: return set_smem_t<NWC, 1>(smem, threads);
-        case 2: return set_smem_t<NWC, 2>(smem, threads);
-        case 4: return set_smem_t<NWC, 4>(smem, threads);
-        default: return set_smem_t<NWC, 8>(smem, threads);
+    switch (group) {
+        case 16: return set_smem_t<NWC, 16>(smem, threads);
+        case 32: return set_smem_t<NWC, 32>(smem, threads);
+        case 64: return set_smem_t<NWC, 64>(smem, threads);
+        case 128: return set_smem_t<NWC, 128>(smem, threads);
+        default: return set_smem_t<NWC, 256>(smem, threads);
+    }
+}
+
+int max_threads_for(int cw)
+{
+    return cw == 1 ? kMaxThreads<1> : cw == 2 ? kMaxThreads<2> : cw == 3 ? kMaxThreads<3> : kMaxThreads<4>;
+}
+
+template <int NWC, int GT>
+cudaError_t launch_multi_t(const LSJob *jobs, int njobs, const LSLaunch &L, cudaStream_t st)
+{
+    local_search_multi_kernel<NWC, GT><<<L.blocks, GT * L.walks, L.smem, st>>>(jobs, njobs, L.walks, L.s_smem);
+    return cudaGetLastError();
+}
+
+template <int NWC>
+cudaError_t launch_multi_g(const LSJob *jobs, int njobs, const LSLaunch &L, cudaStream_t st)
+{
+    switch (L.group) {
+        case 16: return launch_multi_t<NWC, 16>(jobs, njobs, L, st);
+        case 32: return launch_multi_t<NWC, 32>(jobs, njobs, L, st);
+        case 64: return launch_multi_t<NWC, 64>(jobs, njobs, L, st);
+        case 128: return launch_multi_t<NWC, 128>(jobs, njobs, L, st);
+        default: return launch_multi_t<NWC, 256>(jobs, njobs, L, st);
+    }
+}
+
+template <int NWC, int GT>
+int set_smem_multi_t(size_t smem, int threads)
+{
+    cudaFuncSetAttribute(local_search_multi_kernel<NWC, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, local_search_multi_kernel<NWC, GT>, threads, smem) !=
+        cudaSuccess)
+        per_sm = 0;
+    return per_sm;
+}
+
+template <int NWC>
+int set_smem_multi_g(int group, size_t smem, int threads)
+{
+    switch (group) {
+        case 16: return set_smem_multi_t<NWC, 16>(smem, threads);
+        case 32: return set_smem_multi_t<NWC, 32>(smem, threads);
+        case 64: return set_smem_multi_t<NWC, 64>(smem, threads);
+        case 128: return set_smem_multi_t<NWC, 128>(smem, threads);
+        default: return set_smem_multi_t<NWC, 256>(smem, threads);
     }
 }
 
 }  // namespace
 
-SmemPlan smem_plan(const DevInst &I, int warps) { return make_plan(I, warps); }
-
-LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps, int max_walks)
+LSLaunch plan_local_search(const DevInst &I, int device, int count, int group, int max_walks, int s_place)
 {
     LSLaunch L;
-    if (warps <= 0) warps = 1;                     // automatic: one warp per walk
-    L.warps = warps == 1 || warps == 2 || warps == 4 ? warps : 8;
+    L.blocks = 0;
+    L.walks = 0;
+    L.smem = 0;
+    if (group <= 0) group = 32;                    // automatic: one warp per walk
+    L.group = group <= 16 ? 16 : group <= 32 ? 32 : group <= 64 ? 64 : group <= 128 ? 128 : 256;
     L.colour_words = colour_words(I.n);
-    const SmemPlan p = make_plan(I, L.warps);
+    const int warps = L.group < 32 ? 1 : L.group / 32;
     int max_smem = 0, sms = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    // one block per SM holding as many walk slots as fit (at most kMaxThreads
-    // threads: 512 for 64 <= n < 96, 384 from 96, 256 below 64 with two blocks)
-    long long walks = ((long long)max_smem - (long long)p.inst) / (long long)p.slot;
-    const int max_threads = L.colour_words == 1 ? kMaxThreads<1> : L.colour_words == 2 ? kMaxThreads<2>
-                          : L.colour_words == 3 ? kMaxThreads<3> : kMaxThreads<4>;
-    walks = std::min<long long>(walks, std::max(1, max_threads / (32 * L.warps)));
-    if (max_walks > 0) walks = std::min<long long>(walks, max_walks);
-    if (walks < 1) {
-        L.blocks = 0;
-        L.walks = 0;
-        L.smem = 0;
-        return L;
-    }
+    // one block per SM holding as many walk slots as fit (at most the kernel's
+    // thread limit: 512 for 64 <= n < 96, 384 from 96, 256 below 64 with two
+    // blocks); the colouring stays in the slot unless that would cut the walks
+    long long by_threads = std::max(1, max_threads_for(L.colour_words) / L.group);
+    if (max_walks > 0) by_threads = std::min<long long>(by_threads, max_walks);
+    const SmemPlan ps = make_plan(I, warps, true), pg = make_plan(I, warps, false);
+    const long long walks_s = ((long long)max_smem - (long long)ps.inst) / (long long)ps.slot;
+    const long long walks_g = ((long long)max_smem - (long long)pg.inst) / (long long)pg.slot;
+    bool s_smem = s_place == 1 ? true : s_place == 2 ? false : walks_s >= by_threads;
+    long long walks = std::min<long long>(s_smem ? walks_s : walks_g, by_threads);
+    if (walks < 1) return L;
+    const SmemPlan &p = s_smem ? ps : pg;
+    L.s_smem = s_smem ? 1 : 0;
     L.walks = (int)walks;
     L.smem = p.total(L.walks);
-    const int threads = 32 * L.warps * L.walks;
+    const int threads = L.group * L.walks;
     int per_sm = 0;
     switch (L.colour_words) {
-        case 1: per_sm = set_smem_w<1>(L.warps, L.smem, threads); break;
-        case 2: per_sm = set_smem_w<2>(L.warps, L.smem, threads); break;
-        case 3: per_sm = set_smem_w<3>(L.warps, L.smem, threads); break;
-        default: per_sm = set_smem_w<4>(L.warps, L.smem, threads); break;
+        case 1: per_sm = set_smem_g<1>(L.group, L.smem, threads); break;
+        case 2: per_sm = set_smem_g<2>(L.group, L.smem, threads); break;
+        case 3: per_sm = set_smem_g<3>(L.group, L.smem, threads); break;
+        default: per_sm = set_smem_g<4>(L.group, L.smem, threads); break;
     }
     long long blocks = ((long long)count + walks - 1) / walks;
     blocks = std::min<long long>(blocks, (long long)sms * std::max(per_sm, 1));
@@ -1449,14 +1579,70 @@ LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps, i
     return L;
 }
 
+LSLaunch plan_local_search_multi(const DevInst *insts, int count, int device, int group, int max_walks, int s_place)
+{
+    LSLaunch L;
+    if (count <= 0) return L;
+    if (group <= 0) group = 32;
+    L.group = group <= 16 ? 16 : group <= 32 ? 32 : group <= 64 ? 64 : group <= 128 ? 128 : 256;
+    L.colour_words = colour_words(insts[0].n);
+    for (int k = 1; k < count; ++k)
+        if (colour_words(insts[k].n) != L.colour_words) return L;   // one colour-word class per launch
+    const int warps = L.group < 32 ? 1 : L.group / 32;
+    int max_smem = 0, sms = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    // the static part of the kernel's shared memory (job descriptors)
+    const long long budget = (long long)max_smem - (long long)(sizeof(DevInst) + sizeof(LSArgs) + 64);
+    long long by_threads = std::max(1, max_threads_for(L.colour_words) / L.group);
+    if (max_walks > 0) by_threads = std::min<long long>(by_threads, max_walks);
+    long long walks_s = by_threads, walks_g = by_threads;
+    for (int k = 0; k < count; ++k) {
+        const SmemPlan ps = make_plan(insts[k], warps, true), pg = make_plan(insts[k], warps, false);
+        walks_s = std::min<long long>(walks_s, (budget - (long long)ps.inst) / (long long)ps.slot);
+        walks_g = std::min<long long>(walks_g, (budget - (long long)pg.inst) / (long long)pg.slot);
+    }
+    const bool s_smem = s_place == 1 ? true : s_place == 2 ? false : walks_s >= by_threads;
+    const long long walks = s_smem ? walks_s : walks_g;
+    if (walks < 1) return L;
+    L.s_smem = s_smem ? 1 : 0;
+    L.walks = (int)walks;
+    size_t smem = 0;
+    for (int k = 0; k < count; ++k) smem = std::max(smem, make_plan(insts[k], warps, s_smem).total(L.walks));
+    L.smem = smem;
+    const int threads = L.group * L.walks;
+    int per_sm = 0;
+    switch (L.colour_words) {
+        case 1: per_sm = set_smem_multi_g<1>(L.group, L.smem, threads); break;
+        case 2: per_sm = set_smem_multi_g<2>(L.group, L.smem, threads); break;
+        case 3: per_sm = set_smem_multi_g<3>(L.group, L.smem, threads); break;
+        default: per_sm = set_smem_multi_g<4>(L.group, L.smem, threads); break;
+    }
+    L.blocks = per_sm > 0 ? sms * per_sm : 0;
+    return L;
+}
+
+cudaError_t launch_local_search_multi(const LSJob *jobs, int njobs, const LSLaunch &L, cudaStream_t st)
+{
+    if (L.blocks <= 0 || njobs <= 0) return cudaErrorInvalidConfiguration;
+    switch (L.colour_words) {
+        case 1: return launch_multi_g<1>(jobs, njobs, L, st);
+        case 2: return launch_multi_g<2>(jobs, njobs, L, st);
+        case 3: return launch_multi_g<3>(jobs, njobs, L, st);
+        default: return launch_multi_g<4>(jobs, njobs, L, st);
+    }
+}
+
 cudaError_t launch_local_search(const DevInst &I, const LSArgs &a, const LSLaunch &L, cudaStream_t st)
 {
     if (L.blocks <= 0) return cudaErrorInvalidConfiguration;
+    LSArgs b = a;
+    b.s_smem = L.s_smem;
     switch (L.colour_words) {
-        case 1: return launch_w<1>(I, a, L, st);
-        case 2: return launch_w<2>(I, a, L, st);
-        case 3: return launch_w<3>(I, a, L, st);
-        default: return launch_w<4>(I, a, L, st);
+        case 1: return launch_g<1>(I, b, L, st);
+        case 2: return launch_g<2>(I, b, L, st);
+        case 3: return launch_g<3>(I, b, L, st);
+        default: return launch_g<4>(I, b, L, st);
     }
 }
 

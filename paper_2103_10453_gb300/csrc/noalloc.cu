@@ -9,7 +9,8 @@
 // cudaMalloc / cudaFree.  This entry point serves them: it calls no cudaMalloc,
 // cudaFree or allocating library routine.  Its scratch (the evicted-tabu
 // tables, the tabu caches, the candidate lists, the member-id XOR tables, the
-// per-slot clocks, the walk counter and the check flag) lives in
+// colouring buffers, the per-slot clocks, the walk counter and the check flag)
+// lives in
 // the file-scope array below, kNoAllocScratchBytes bytes on every GPU that loads
 // the library, held until the process exits.
 //
@@ -86,29 +87,32 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
 
     // walk slots that fit: each needs an evicted-tabu table (4 * |V| * n1p bytes),
     // a tabu cache (8 * |V| bytes), a candidate list (2 * |V| bytes), a member-id
-    // XOR table (4 * n * n1p bytes), the high colour-count planes and a clock word
+    // XOR table (4 * n * n1p bytes), the high colour-count planes, a colouring
+    // buffer (|V| rounded up to 16 bytes) and a clock word
     const size_t xr_bytes = 4 * (size_t)h->di.n * h->di.n1p;
     const size_t hp_bytes = 4 * hp_words(h->di);
-    const size_t table_bytes = 4 * (size_t)h->di.nv * h->di.n1p + 10 * (size_t)h->di.nv + xr_bytes + hp_bytes;
+    const size_t sw = sw_bytes(h->di);
+    const size_t table_bytes =
+        4 * (size_t)h->di.nv * h->di.n1p + 10 * (size_t)h->di.nv + xr_bytes + hp_bytes + sw;
     const size_t max_slots = (kNoAllocScratchBytes - kCounterBytes - 1536) / (table_bytes + 4);   // 1536: alignment
     if (max_slots < 1)
         return fail(h, PLSE_ENOTSUP,
                     "plse_local_search_noalloc: one walk slot needs %zu bytes of scratch, more than the %zu "
                     "available", table_bytes + 4, kNoAllocScratchBytes - kCounterBytes);
-    LSLaunch L = plan_local_search(h->di, device, count, h->ls_warps, h->ls_walks);
+    LSLaunch L = plan_local_search(h->di, device, count, h->ls_lanes, h->ls_walks, h->ls_splace);
     if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: local search does not fit");
     if ((size_t)L.slots() > max_slots) {
         if ((size_t)L.walks > max_slots) {
             const int cap = h->ls_walks > 0 ? std::min(h->ls_walks, (int)max_slots) : (int)max_slots;
-            L = plan_local_search(h->di, device, count, h->ls_warps, cap);
+            L = plan_local_search(h->di, device, count, h->ls_lanes, cap, h->ls_splace);
         }
         L.blocks = (int)std::min<size_t>((size_t)L.blocks, max_slots / (size_t)L.walks);
         if (L.blocks <= 0) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: no walk slot fits");
     }
     const size_t slots = (size_t)L.slots();
     // layout: [counters][slot clocks][evicted-tabu tables][tabu caches][lists][XOR
-    // tables][high planes]; the first three must start at zero, the rest is rebuilt
-    // by every phase
+    // tables][high planes][colourings]; the first three must start at zero, the
+    // rest is rebuilt by every walk
     int *counters = reinterpret_cast<int *>(scratch);
     uint32_t *clocks = reinterpret_cast<uint32_t *>(scratch + kCounterBytes);
     const size_t tables_off = (kCounterBytes + 4 * slots + 255) & ~size_t(255);
@@ -121,7 +125,9 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     uint16_t *xrs = reinterpret_cast<uint16_t *>(scratch + xr_off);
     const size_t hp_off = (xr_off + slots * xr_bytes + 255) & ~size_t(255);
     uint32_t *hps = reinterpret_cast<uint32_t *>(scratch + hp_off);
-    const size_t used = hp_off + slots * hp_bytes;
+    const size_t sw_off = (hp_off + slots * hp_bytes + 255) & ~size_t(255);
+    uint8_t *sws = scratch + sw_off;
+    const size_t used = sw_off + slots * sw;
     if (used > kNoAllocScratchBytes) return fail(h, PLSE_ENOTSUP, "plse_local_search_noalloc: scratch overflow");
     e = cudaMemsetAsync(scratch, 0, tc_off, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "plse_local_search_noalloc: clear scratch");
@@ -155,6 +161,7 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     a.LIST = lists;
     a.XR = xrs;
     a.HP = hps;
+    a.SW = sws;
     a.slot_clock = clocks;
     a.work_counter = counters;
     a.error_flag = counters + 1;

@@ -59,27 +59,37 @@ struct LSArgs {
     uint16_t *LIST;               // [slots][nv] candidate lists
     uint16_t *XR;                 // [slots][2n][n1p] member-id XOR per line and colour
     uint32_t *HP;                 // [slots][2n][cw][8] colour-count planes 2..6
+    uint8_t *SW;                  // [slots][nv rounded up to 16] current colourings (when not
+                                  // kept in shared memory)
     uint32_t *slot_clock;         // [slots] next free clock value of each slot
     int *work_counter;            // dynamic walk scheduler, zeroed before launch
     int *error_flag;              // nonzero after a failed device bound check
     const int *skip;              // if non-null and nonzero at launch: return at once
+    int s_smem;                   // set by the launcher: colourings in shared memory
 };
 
 struct LSLaunch {
-    int blocks;        // persistent blocks (one per SM at most)
-    int warps;         // warps per walk (1, 2, 4 or 8)
-    int walks;         // concurrent walks per block, each with its own shared-memory slot
-    size_t smem;       // dynamic shared memory per block
-    int colour_words;  // 32-bit words of a colour mask actually used (1..4)
+    int blocks = 0;      // persistent blocks (one per SM at most, two below n = 64)
+    int group = 32;      // threads per walk (16: two walks per warp; 32, 64, 128, 256)
+    int walks = 0;       // concurrent walks per block, each with its own shared-memory slot
+    size_t smem = 0;     // dynamic shared memory per block
+    int colour_words = 1;// 32-bit words of a colour mask actually used (1..4)
+    int s_smem = 1;      // current colourings in the shared-memory slots (else global)
     int slots() const { return blocks * walks; }
 };
 
 // Shared-memory plan of one block (bytes): instance part, then `walks` slots.
 struct SmemPlan {
     size_t inst;       // vertex coordinates, allowed-colour masks and line lengths
-    size_t slot;       // one walk: colouring, count words (planes 0-1, high OR), candidate masks, scalars
-    size_t off_S, off_RP, off_KP, off_cmask, off_lmask, off_red;   // within a slot
+    size_t slot;       // one walk: [colouring], count planes 0-1, high OR, candidate masks, scalars
+    size_t off_S, off_P01, off_PH, off_cmask, off_lmask, off_red;   // within a slot
     size_t total(int walks) const { return inst + slot * (size_t)walks; }
+};
+
+// One job of a multi-instance local-search launch.
+struct LSJob {
+    DevInst I;
+    LSArgs a;
 };
 
 // Launchers (return cudaError_t of the launch; asynchronous).
@@ -87,11 +97,25 @@ cudaError_t launch_init_population(const DevInst &I, int pop, uint64_t seed, uin
                                    cudaStream_t st);
 cudaError_t launch_local_search(const DevInst &I, const LSArgs &a, const LSLaunch &L,
                                 cudaStream_t st);
-// warps = 0: automatic.  max_walks caps the walks per block (0 = no cap).
-LSLaunch plan_local_search(const DevInst &I, int device, int count, int warps, int max_walks = 0);
+// group = threads per walk (0: automatic); max_walks caps the walks per block
+// (0 = no cap); s_place: 0 = colourings in shared memory unless that cuts the
+// walks per block, 1 = shared memory, 2 = global memory.
+LSLaunch plan_local_search(const DevInst &I, int device, int count, int group, int max_walks = 0,
+                           int s_place = 0);
+// One persistent launch over `count` instances of one colour-word class: as many
+// blocks as are resident, walks per block and shared memory fitting the largest
+// instance.  blocks = 0 if the instances differ in class or nothing fits.
+LSLaunch plan_local_search_multi(const DevInst *insts, int count, int device, int group, int max_walks = 0,
+                                 int s_place = 0);
+// jobs: device array [njobs]; each job's work counter must be zero at launch and
+// each job's scratch must hold L.slots() walk slots.
+cudaError_t launch_local_search_multi(const LSJob *jobs, int njobs, const LSLaunch &L, cudaStream_t st);
 
 // 32-colour words of a colour mask over colours 0..n
 __host__ __device__ inline int colour_words(int n) { return n < 32 ? 1 : n < 64 ? 2 : n < 96 ? 3 : 4; }
+
+// bytes per walk slot of the global colouring buffer
+inline size_t sw_bytes(const DevInst &I) { return ((size_t)I.nv + 15) & ~size_t(15); }
 
 // u32 words per walk slot of the colour-count planes 2..6 kept in global memory
 // ([2n lines][colour words][8])

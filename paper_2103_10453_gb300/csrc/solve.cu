@@ -192,10 +192,10 @@ __global__ void init_ctrl_kernel(Ctrl *ctrl, int nv, int ftarget)
 template <typename T>
 int dalloc(plse_instance *h, T *&p, size_t n, cudaStream_t st)
 {
-    if (p) { dev_free(p, st); p = nullptr; }
+    if (p) { h_free(h, p, st); p = nullptr; }
     if (n == 0) n = 1;
     void *q = nullptr;
-    cudaError_t e = dev_malloc(&q, n * sizeof(T), st);
+    cudaError_t e = h_malloc(h, &q, n * sizeof(T), st);
     if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "solver allocation: %s", cudaGetErrorString(e));
     p = static_cast<T *>(q);
     return PLSE_OK;
@@ -205,21 +205,21 @@ static_assert(2 * kGenDepth <= 4, "the host flag slot holds two generations");
 
 }  // namespace
 
-void free_pop_scratch(PopScratch &ps, cudaStream_t st);
+void free_pop_scratch(plse_instance *h, PopScratch &ps, cudaStream_t st);
 
 namespace {
 
 // device buffers, events and the pinned flag slot of a solver state
-void free_solver_state(SolverState *s, cudaStream_t st)
+void free_solver_state(plse_instance *h, SolverState *s, cudaStream_t st)
 {
     for (int k = 0; k < 2; ++k) {
-        dev_free(s->Pall[k], st); dev_free(s->planes[k], st); dev_free(s->e[k], st);
-        dev_free(s->uid[k], st); dev_free(s->tested[k], st); dev_free(s->tcount[k], st);
+        h_free(h, s->Pall[k], st); h_free(h, s->planes[k], st); h_free(h, s->e[k], st);
+        h_free(h, s->uid[k], st); h_free(h, s->tested[k], st); h_free(h, s->tcount[k], st);
     }
-    dev_free(s->SO, st); dev_free(s->fprime, st); dev_free(s->sel, st); dev_free(s->partner, st);
-    dev_free(s->dist, st); dev_free(s->wstats, st); dev_free(s->ctrl, st); dev_free(s->Sstar, st);
-    dev_free(s->trace, st);
-    free_pop_scratch(s->ps, st);
+    h_free(h, s->SO, st); h_free(h, s->fprime, st); h_free(h, s->sel, st); h_free(h, s->partner, st);
+    h_free(h, s->dist, st); h_free(h, s->wstats, st); h_free(h, s->ctrl, st); h_free(h, s->Sstar, st);
+    h_free(h, s->trace, st);
+    free_pop_scratch(h, s->ps, st);
     for (auto &ev : s->ev) if (ev) cudaEventDestroy(ev);
     for (auto &g : s->gev)
         for (auto &ev : g) if (ev) cudaEventDestroy(ev);
@@ -242,22 +242,41 @@ int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p, cudaStream_t st)
     return PLSE_OK;
 }
 
-void free_pop_scratch(PopScratch &ps, cudaStream_t st)
+void free_pop_scratch(plse_instance *h, PopScratch &ps, cudaStream_t st)
 {
-    dev_free(ps.order, st); dev_free(ps.mind, st); dev_free(ps.acc, st); dev_free(ps.rej, st);
-    dev_free(ps.Dloc, st); dev_free(ps.sel_state, st);
+    h_free(h, ps.order, st); h_free(h, ps.mind, st); h_free(h, ps.acc, st); h_free(h, ps.rej, st);
+    h_free(h, ps.Dloc, st); h_free(h, ps.sel_state, st);
     ps = PopScratch();
 }
 
 void release_solver(plse_instance *h, cudaStream_t st)
 {
-    if (h->solver) free_solver_state(h->solver, st);
+    if (h->solver) free_solver_state(h, h->solver, st);
     h->solver = nullptr;
     // step scratch
-    dev_free(h->step_planes, st);
+    h_free(h, h->step_planes, st);
     h->step_planes = nullptr;
     h->step_planes_cap = 0;
-    free_pop_scratch(h->step_ps, st);
+    free_pop_scratch(h, h->step_ps, st);
+}
+
+// Device bytes ensure_solver takes for a run of p individuals and `gens`
+// generations, each buffer rounded up as the bound-workspace allocator does.
+size_t solver_bytes(const plse_instance *h, int p, int gens)
+{
+    const DevInst &I = h->di;
+    const size_t PV = (size_t)p * I.nv, stride = (size_t)I.nw * I.nb, cap = (size_t)h->params.tested_cap;
+    auto a = [](size_t bytes) { return ws_align(bytes ? bytes : 1); };
+    size_t t = 0;
+    for (int k = 0; k < 2; ++k)
+        t += a(2 * PV) + a(4 * 2 * (size_t)p * stride) + a(8 * 2 * (size_t)p) + a(4 * (size_t)p) +
+             a(4 * (size_t)p * cap) + a(4 * (size_t)p);
+    t += a(PV) + 4 * a(4 * (size_t)p) + a(sizeof(plse_walk_stats) * (size_t)p) + a(sizeof(Ctrl)) +
+         a((size_t)I.nv) + a(4 * (size_t)gens);
+    const int m = 2 * p, nchunks = (m + kChunk - 1) / kChunk;
+    t += a(4 * (size_t)m) + a(4 * (size_t)m) + a(4 * (size_t)p) + a(4 * (size_t)m) +
+         a(2 * (size_t)nchunks * kChunk * kChunk) + a(sizeof(SelState));
+    return t;
 }
 
 static int ensure_solver(plse_instance *h, int p, int gens, cudaStream_t st)
@@ -267,7 +286,7 @@ static int ensure_solver(plse_instance *h, int p, int gens, cudaStream_t st)
     if (s && s->cap_p >= p && s->cap_gens >= gens && s->tested_cap == cap) return PLSE_OK;
     if (s) {
         // keep the step scratch, rebuild the solver buffers
-        free_solver_state(s, st);
+        free_solver_state(h, s, st);
         h->solver = nullptr;
     }
     s = new SolverState();
@@ -374,34 +393,51 @@ static bool partial_mpma(const plse_instance *h)
 // host memory, then Alg. 4, gather, matching and crossover.  If the bound is
 // reached in this or an earlier generation, every later kernel returns at
 // entry, so generations enqueued past the stop leave no trace in the results.
-static int issue_generation(plse_instance *h)
+struct GenPlan {
+    int p, g, cur, nxt, slot, flags;
+    size_t PV;
+    const int *skip;
+    uint8_t *Pp;
+};
+
+static GenPlan plan_generation(plse_instance *h)
+{
+    Session &se = h->session;
+    SolverState *s = h->solver;
+    const plse_params &prm = h->params;
+    GenPlan q;
+    q.p = se.pop;
+    q.g = se.issued;
+    q.cur = se.cur;
+    q.nxt = q.cur ^ 1;
+    q.slot = q.g % kGenDepth;
+    q.PV = (size_t)q.p * h->nv;
+    q.skip = prm.stop_at_bound ? &s->ctrl->done : nullptr;
+    q.flags = partial_mpma(h) ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
+                              : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
+    q.Pp = s->Pall[q.cur] + q.PV;
+    return q;
+}
+
+// the generation after its local search: best update, Alg. 4, matching, AUX
+static int issue_generation_rest(plse_instance *h, const GenPlan &q)
 {
     Session &se = h->session;
     SolverState *s = h->solver;
     const cudaStream_t st = se.stream;
     const DevInst &I = h->di;
     const plse_params &prm = h->params;
-    const int nv = h->nv;
-    const int ftarget = h->l == 1 ? 1 : 0;
-    const int p = se.pop, cap = prm.tested_cap, g = se.issued, cur = se.cur, nxt = cur ^ 1;
-    const int slot = g % kGenDepth;
-    const size_t PV = (size_t)p * nv, stride = (size_t)I.nw * I.nb;
-    const int *skip = prm.stop_at_bound ? &s->ctrl->done : nullptr;
-    const int flags = partial_mpma(h) ? (PLSE_LS_REPAIR | PLSE_LS_PARTIALCOL)
-                                      : (PLSE_LS_PHASE1 | PLSE_LS_PHASE2 | PLSE_LS_REPAIR);
-    uint8_t *Pp = s->Pall[cur] + PV;
-    StreamScope scope(h, st);
-    CK(cudaEventRecord(s->gev[slot][0], st));
-    int rc = enqueue_local_search(h, s->SO, Pp, p, 0, g, se.iters, se.seed, flags, s->fprime, nullptr,
-                                  s->wstats, st, skip);
-    if (rc) return rc;
-    CK(cudaEventRecord(s->gev[slot][1], st));
-    best_kernel<<<1, 1024, 0, st>>>(p, nv, ftarget, g, prm.stop_at_bound, s->fprime, Pp, s->wstats,
+    const int nv = h->nv, ftarget = h->l == 1 ? 1 : 0;
+    const int p = q.p, g = q.g, cur = q.cur, nxt = q.nxt, cap = prm.tested_cap;
+    const size_t stride = (size_t)I.nw * I.nb;
+    const int *skip = q.skip;
+    CK(cudaEventRecord(s->gev[q.slot][1], st));
+    best_kernel<<<1, 1024, 0, st>>>(p, nv, ftarget, g, prm.stop_at_bound, s->fprime, q.Pp, s->wstats,
                                     s->e[cur] + p, s->ctrl, s->Sstar, s->trace);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(s->hflag + 2 * slot, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaEventRecord(s->gev[slot][2], st));
-    CK(launch_planes(I, Pp, p, s->planes[cur] + (size_t)p * stride, st));
+    CK(cudaMemcpyAsync(s->hflag + 2 * q.slot, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(s->gev[q.slot][2], st));
+    CK(launch_planes(I, q.Pp, p, s->planes[cur] + (size_t)p * stride, st));
     CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st));
     gather_kernel<<<(p * 32 + 255) / 256, 256, 0, st>>>(
         I, p, g, s->sel, s->Pall[cur], s->planes[cur], s->e[cur], s->uid[cur], s->tested[cur], s->tcount[cur],
@@ -415,6 +451,51 @@ static int issue_generation(plse_instance *h)
     se.cur = nxt;
     se.issued = g + 1;
     return PLSE_OK;
+}
+
+// Enqueues generation se.issued on the run's stream.  Every kernel returns at
+// entry once the bound is reached (the skip flag), so generations enqueued past
+// the stop leave no trace in the results.
+static int issue_generation(plse_instance *h)
+{
+    Session &se = h->session;
+    SolverState *s = h->solver;
+    const cudaStream_t st = se.stream;
+    const GenPlan q = plan_generation(h);
+    StreamScope scope(h, st);
+    CK(cudaEventRecord(s->gev[q.slot][0], st));
+    int rc = enqueue_local_search(h, s->SO, q.Pp, q.p, 0, q.g, se.iters, se.seed, q.flags, s->fprime, nullptr,
+                                  s->wstats, st, q.skip);
+    if (rc) return rc;
+    return issue_generation_rest(h, q);
+}
+
+int generation_head(plse_instance *h, int slots, LSArgs &a, cudaEvent_t *ready)
+{
+    Session &se = h->session;
+    if (!se.active || se.finished || se.issued >= se.max_gens || !h->solver)
+        return fail(h, PLSE_ENOTSUP, "no generation to issue");
+    SolverState *s = h->solver;
+    const cudaStream_t st = se.stream;
+    const GenPlan q = plan_generation(h);
+    StreamScope scope(h, st);
+    int rc = ensure_ls_workspace(h, slots, st);
+    if (rc) return rc;
+    a = ls_args(h, s->SO, q.Pp, q.p, 0, q.g, se.iters, se.seed, q.flags, s->fprime, nullptr, s->wstats, q.skip);
+    CK(cudaMemsetAsync(a.work_counter, 0, sizeof(int), st));
+    CK(cudaEventRecord(s->gev[q.slot][0], st));
+    *ready = s->gev[q.slot][0];
+    return PLSE_OK;
+}
+
+int generation_tail(plse_instance *h, cudaEvent_t ls_done)
+{
+    Session &se = h->session;
+    const cudaStream_t st = se.stream;
+    const GenPlan q = plan_generation(h);
+    StreamScope scope(h, st);
+    CK(cudaStreamWaitEvent(st, ls_done, 0));
+    return issue_generation_rest(h, q);
 }
 
 int run_issue(plse_instance *h, int *issued)
@@ -605,6 +686,23 @@ int plse_run_query(plse_handle h, int *done, int *generations, int *in_flight)
     if (done) *done = se.finished && se.polled == se.issued;
     if (generations) *generations = se.gen;
     if (in_flight) *in_flight = se.issued - se.polled;
+    return PLSE_OK;
+}
+
+int plse_run_population(plse_handle h, int which, uint8_t *dst, void *stream)
+{
+    if (!h || !dst || (which != PLSE_RUN_POPULATION && which != PLSE_RUN_OFFSPRING)) return PLSE_EINVAL;
+    Session &se = h->session;
+    if (!se.active || !h->solver) return fail(h, PLSE_EINVAL, "plse_run_population: no run in progress");
+    int rc = run_drain(h);
+    if (rc) return rc;
+    const cudaStream_t st = (cudaStream_t)stream;
+    StreamScope scope(h, st);
+    SolverState *s = h->solver;
+    const size_t bytes = (size_t)se.pop * h->nv;
+    const uint8_t *src = which == PLSE_RUN_POPULATION ? s->Pall[se.cur] : s->SO;
+    if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
     return PLSE_OK;
 }
 

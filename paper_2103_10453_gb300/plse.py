@@ -60,7 +60,8 @@ class Job(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("best_score", C.c_int32), ("stats", SolveStats),
-                ("ms_queue", C.c_double), ("ms_wall", C.c_double), ("detail", C.c_char * 128)]
+                ("ms_queue", C.c_double), ("ms_wall", C.c_double), ("detail", C.c_char * 128),
+                ("mem_bytes", C.c_int64)]
 
     def as_dict(self):
         st = self.stats
@@ -69,7 +70,7 @@ class Result(C.Structure):
                 "walks": st.walks.as_dict(), "ms_total": float(st.ms_total),
                 "ms_local_search": float(st.ms_local_search), "launches": int(st.launches),
                 "ms_queue": float(self.ms_queue), "ms_wall": float(self.ms_wall),
-                "detail": self.detail.decode(errors="replace")}
+                "detail": self.detail.decode(errors="replace"), "mem_bytes": int(self.mem_bytes)}
 
 
 _lib = None
@@ -83,7 +84,11 @@ SIGNATURES = {
     "plse_last_error_detail": (C.c_int, [_vp, C.c_char_p, C.c_size_t]),
     "plse_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "plse_sync": (C.c_int, [_vp, _vp]),
-    "plse_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "plse_autotune": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "plse_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "plse_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "plse_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "plse_default_params": (None, [C.POINTER(Params)]),
     "plse_set_params": (C.c_int, [_vp, C.POINTER(Params)]),
     "plse_get_params": (C.c_int, [_vp, C.POINTER(Params)]),
@@ -94,16 +99,19 @@ SIGNATURES = {
     "plse_run_step": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
     "plse_run_result": (C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int), C.POINTER(SolveStats), _vp]),
     "plse_run_issue": (C.c_int, [_vp, _vp, C.POINTER(C.c_int)]),
+    "plse_run_population": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "plse_run_query": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "plse_solve_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(Job), C.c_int, C.c_int, C.POINTER(_vp),
                                    C.POINTER(Result)]),
-    "plse_server_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_vp)]),
+    "plse_server_create": (C.c_int, [C.c_int, C.c_int, C.c_size_t, C.POINTER(_vp)]),
+    "plse_server_memory": (C.c_int, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                     C.POINTER(C.c_size_t), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "plse_server_submit": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(Job), C.POINTER(Params),
                                      C.POINTER(C.c_int64)]),
     "plse_server_poll": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, C.POINTER(Result)]),
     "plse_server_cancel": (C.c_int, [_vp, C.c_int64]),
     "plse_server_pending": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
-    "plse_server_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "plse_server_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "plse_server_destroy": (None, [_vp]),
     "plse_init_population": (C.c_int, [_vp, C.c_int, _u64, _vp, _vp]),
     "plse_local_search": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _i64, _u64, C.c_int,
@@ -209,13 +217,40 @@ class Instance:
         self._check(self.lib.plse_get_params(self.h, C.byref(p)))
         return p
 
-    def set_launch(self, ls_warps: int = 0, ls_walks: int = 0):
-        """Warps per walk and walks per block of the local-search kernel (results
-        do not depend on them)."""
-        self._check(self.lib.plse_set_launch(self.h, ls_warps, ls_walks))
+    def set_launch(self, ls_lanes: int = 0, ls_walks: int = 0, ls_colourings: int = 0):
+        """Threads per walk, walks per block and colouring placement of the
+        local-search kernel (results do not depend on them)."""
+        self._check(self.lib.plse_set_launch(self.h, ls_lanes, ls_walks, ls_colourings))
 
     def sync(self, stream=None):
         self._check(self.lib.plse_sync(self.h, _stream(stream)))
+
+    def autotune(self, pop: int, probe_iters: int = 200):
+        """Times probe launches and applies the fastest local-search launch knobs
+        for runs of ``pop`` individuals (plse_autotune); returns
+        (lanes, walks, colourings, probe moves/s)."""
+        l, w, c, r = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        self._check(self.lib.plse_autotune(self.h, pop, probe_iters, C.byref(l), C.byref(w), C.byref(c),
+                                           C.byref(r)))
+        return l.value, w.value, c.value, r.value
+
+    # ---- caller-supplied device memory ------------------------------------
+    def workspace_size(self, pop: int, max_generations: int) -> int:
+        """Device bytes a run of ``pop`` individuals and ``max_generations``
+        generations takes (plse_workspace_size)."""
+        out = C.c_size_t(0)
+        self._check(self.lib.plse_workspace_size(self.h, pop, max_generations, C.byref(out)))
+        return int(out.value)
+
+    def bind_workspace(self, buf=None, nbytes=None):
+        """Carves the handle's run and scratch buffers out of ``buf`` (a CUDA
+        tensor, kept alive by the caller) instead of the library's pool; None
+        unbinds (plse_bind_workspace)."""
+        if buf is None:
+            self._check(self.lib.plse_bind_workspace(self.h, None, 0))
+            return
+        nbytes = buf.numel() * buf.element_size() if nbytes is None else nbytes
+        self._check(self.lib.plse_bind_workspace(self.h, C.c_void_p(buf.data_ptr()), nbytes))
 
     # ---- whole solve -----------------------------------------------------
     def solve(self, pop, generations, iters, seed, stream=None, with_stats=False):
@@ -235,11 +270,23 @@ class Instance:
     # ---- resumable run ---------------------------------------------------
     def run_begin(self, pop, max_generations, iters, seed, stream=None):
         self._check(self.lib.plse_run_begin(self.h, pop, max_generations, int(iters), seed, _stream(stream)))
+        self._run_pop = pop
 
     def run_step(self, generations=1, stream=None) -> bool:
         done = C.c_int()
         self._check(self.lib.plse_run_step(self.h, generations, _stream(stream), C.byref(done)))
         return bool(done.value)
+
+    def run_population(self, which=1, out=None, stream=None):
+        """The run's population P_t (which=0) or its next offspring S^O (which=1)
+        as a host array [pop, nv], or copied into the CUDA tensor ``out``."""
+        pop = self._run_pop
+        if out is None:
+            buf = np.zeros((pop, max(self.nv, 1)), dtype=np.uint8)
+            self._check(self.lib.plse_run_population(self.h, which, buf.ctypes.data, _stream(stream)))
+            return buf[:, :self.nv]
+        self._check(self.lib.plse_run_population(self.h, which, C.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
 
     def run_issue(self, stream=None) -> bool:
         """Enqueues the run's next generation without waiting (plse_run_issue)."""
@@ -328,13 +375,15 @@ def solve_batch(instances, jobs, max_inflight=0):
 
 
 class Server:
-    """plse_server_*: requests admitted into `max_inflight` concurrent runs on
-    the current device, served by the library's own host thread."""
+    """plse_server_*: requests admitted into at most `max_inflight` concurrent
+    runs on the current device while their device memory fits `mem_budget`
+    bytes (0: 90% of the free memory at creation), served by the library's own
+    host thread."""
 
-    def __init__(self, max_inflight=8, max_queue=1024):
+    def __init__(self, max_inflight=8, max_queue=1024, mem_budget=0):
         self.lib = load()
         h = C.c_void_p()
-        rc = self.lib.plse_server_create(max_inflight, max_queue, C.byref(h))
+        rc = self.lib.plse_server_create(max_inflight, max_queue, int(mem_budget), C.byref(h))
         if rc != PLSE_OK:
             raise PlseError(rc, "plse_server_create")
         self.h = h
@@ -367,13 +416,24 @@ class Server:
         d["best_grid"] = grid
         return d
 
+    def memory(self):
+        """Admission by device memory: budget, bytes held now, peak bytes held,
+        peak concurrent runs, admissions that waited for memory."""
+        b, u, pk = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        pr, w = C.c_int(), C.c_int64()
+        rc = self.lib.plse_server_memory(self.h, C.byref(b), C.byref(u), C.byref(pk), C.byref(pr), C.byref(w))
+        if rc != PLSE_OK:
+            raise PlseError(rc, "plse_server_memory")
+        return {"budget": b.value, "in_use": u.value, "peak": pk.value, "peak_running": pr.value,
+                "waited_for_memory": w.value}
+
     def cancel(self, ticket):
         rc = self.lib.plse_server_cancel(self.h, ticket)
         if rc != PLSE_OK:
             raise PlseError(rc, "plse_server_cancel")
 
-    def set_launch(self, ls_warps=0, ls_walks=0):
-        rc = self.lib.plse_server_set_launch(self.h, ls_warps, ls_walks)
+    def set_launch(self, ls_lanes=0, ls_walks=0, ls_colourings=0):
+        rc = self.lib.plse_server_set_launch(self.h, ls_lanes, ls_walks, ls_colourings)
         if rc != PLSE_OK:
             raise PlseError(rc, "plse_server_set_launch")
 

@@ -184,3 +184,80 @@ def test_server_mixed_sizes_against_solve_alone(plse):
     for g, job, r in zip(gs, jobs, outs):
         assert r["status"] == 0, r["detail"]
         same(r, alone(plse, g, job))
+
+
+def test_server_admits_by_device_memory(plse):
+    """A budget of 1.5 requests' footprint: requests wait for memory, never two
+    run at once, every result equals plse_solve alone, and a request larger than
+    the budget completes with PLSE_ENOMEM."""
+    gs = [inputs.random_insertion(30, 0.5, 100 + k) for k in range(5)]
+    jobs = [(128, 3, 200, 1 + k) for k in range(5)]
+    probe = plse.Server(max_inflight=4, max_queue=16)
+    one = probe.poll(probe.submit(gs[0], *jobs[0]), wait_ms=-1)
+    probe.close()
+    assert one["status"] == 0 and one["mem_bytes"] > 128 * 450
+    budget = one["mem_bytes"] * 3 // 2
+    srv = plse.Server(max_inflight=4, max_queue=16, mem_budget=budget)
+    tickets = [srv.submit(g, *job) for g, job in zip(gs, jobs)]
+    big = srv.submit(gs[0], 512, 3, 200, 9)        # about 4x the footprint: never fits
+    outs = [srv.poll(t, wait_ms=-1) for t in tickets]
+    rbig = srv.poll(big, wait_ms=-1)
+    mem = srv.memory()
+    srv.close()
+    assert rbig["status"] == plse.PLSE_ENOMEM
+    assert mem["budget"] == budget and mem["in_use"] == 0
+    assert one["mem_bytes"] <= mem["peak"] <= budget
+    assert mem["peak_running"] == 1 and mem["waited_for_memory"] >= 1
+    for g, job, r in zip(gs, jobs, outs):
+        assert r["status"] == 0, r["detail"]
+        assert r["mem_bytes"] == one["mem_bytes"]
+        same(r, alone(plse, g, job))
+
+
+def test_batch_one_launch_per_generation_and_class(plse, oracle_mod):
+    """Distinct handles and no cap on runs in flight: the generations of all runs
+    share one persistent multi-instance local-search launch per colour-word class
+    (here n = 10..25, 40, 70: three classes, uneven populations and stops).
+    Every result equals plse_solve alone, and one equals the oracle's Alg. 2."""
+    gs = grids() + [inputs.random_insertion(40, 0.6, 21), inputs.cyclic_delete(45, 0.7, 22)[0],
+                    inputs.random_insertion(70, 0.7, 23)]
+    jobs = JOBS + [(80, 3, 400, 8), (50, 4, 300, 9), (70, 2, 500, 10)]
+    insts = [plse.Instance(g) for g in gs]
+    out, rc = plse.solve_batch(insts, jobs)
+    assert rc == plse.PLSE_OK
+    for g, job, r in zip(gs, jobs, out):
+        assert r["status"] == 0, r["detail"]
+        same(r, alone(plse, g, job))
+    ref = oracle_mod.Instance(gs[2]).solve(*jobs[2])
+    assert out[2]["score"] == ref["score"] and np.array_equal(out[2]["best_grid"], ref["best_grid"])
+    assert out[2]["walks"] == ref["stats"]
+    for G in insts:
+        G.close()
+
+
+def test_autotune_picks_knobs_without_changing_results(plse, oracle_mod):
+    import torch
+    from _gpu import dev, empty, host
+    grid = inputs.random_insertion(40, 0.5, 31)
+    G, I = plse.Instance(grid), oracle_mod.Instance(grid)
+    P = I.init_population(200, 4)
+    flags = plse.LS_PHASE1 | plse.LS_PHASE2 | plse.LS_REPAIR
+
+    def run():
+        out = empty(P.shape, torch.uint8)
+        st = empty((P.shape[0], 7), torch.int64)
+        G.local_search(dev(P), out, P.shape[0], 3, 2, 600, 9, flags, None, None, st)
+        G.sync()
+        return host(out), host(st)
+
+    before = run()
+    lanes, walks, place, rate = G.autotune(200, probe_iters=100)
+    assert lanes in (16, 32, 64, 128) and place in (0, 1, 2) and rate > 0
+    assert G.autotune(200, probe_iters=100)[:3] == (lanes, walks, place)     # cached
+    after = run()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    So, _, _ = I.tabu_walk(P[0], 3, 2, 1, 600, 9)
+    So, _, _ = I.tabu_walk(So, 3, 2, 2, 2 * I.nv, 9)
+    So, _ = I.repair(So)
+    assert np.array_equal(after[0][0], So)
+    G.close()

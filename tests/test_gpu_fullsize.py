@@ -115,3 +115,68 @@ def test_full_population_update_properties(plse, oracle_mod):
     # the accepted list is in rank order (e, then index)
     key = e[acc] * (2 * p) + acc
     assert (np.diff(key) > 0).all()
+
+
+@pytest.mark.parametrize("r, samples", [(0.3, (3, 7777, 16380)), (0.7, (0, 9001, 16383))])
+def test_steady_state_generation_of_the_benchmark(plse, oracle_mod, r, samples):
+    """The launch the benchmark times: generation 3 of a run at n = 70 and
+    p = 16384, whose walks start from AUX offspring of legal parents (Alg. 2,
+    Alg. 5).  Three generations run through the resumable run API; its offspring
+    S^O then go through plse_local_search with the run's own arguments (ind0 0,
+    generation 3, 10|V| phase-1 iterations, seed 1), and sampled walks are
+    compared with the oracle bit for bit."""
+    import torch
+    grid = inputs.n70(r)
+    G, I = plse.Instance(grid), oracle_mod.Instance(grid)
+    G.set_params(plse.default_params(stop_at_bound=0))
+    pop, iters, seed = 16384, 10 * G.nv, 1
+    G.run_begin(pop, 4, iters, seed)
+    G.run_step(3)
+    SO = G.run_population(1, out=empty((pop, G.nv), torch.uint8))
+    out = empty((pop, G.nv), torch.uint8)
+    F = empty((pop,), torch.int64)
+    st = empty((pop, 7), torch.int64)
+    flags = plse.LS_PHASE1 | plse.LS_PHASE2 | plse.LS_REPAIR
+    G.local_search(SO, out, pop, 0, 3, iters, seed, flags, None, F, st)
+    G.sync()
+    S0, S, F, st = host(SO), host(out), host(F), host(st)
+    # steady state: the parents were legal, so an offspring is far from random
+    assert all(conflicts(I, grid, S0[w]) < G.nv // 4 for w in samples)
+    for w in samples:
+        So, Fo, sto = oracle_generation(I, S0[w], w, 3, iters, seed)
+        assert np.array_equal(S[w], So), (r, w)
+        assert F[w] == Fo
+        assert st[w].tolist() == [sto[k] for k in FIELDS], (r, w)
+    # the run's own fourth generation consumed the same offspring
+    G.run_step(1)
+    res = G.run_result()
+    assert res["generations"] == 4
+    G.close()
+
+
+def test_pop_update_past_sixteen_chunks_bit_exact(plse, oracle_mod):
+    """Alg. 4 over 2p = 4096 candidates (32 chunks of 128): P_t of a run after
+    two generations and the legal local-search results of its offspring, scored
+    e = f + |V| c, against the oracle on its own 4096 x 4096 distance matrix."""
+    import torch
+    grid = inputs.random_insertion(30, 0.5, 2024)
+    G, I = plse.Instance(grid), oracle_mod.Instance(grid)
+    G.set_params(plse.default_params(stop_at_bound=0))
+    p = 2048
+    G.run_begin(p, 3, 4 * G.nv, 7)
+    G.run_step(2)
+    Pt = G.run_population(0)
+    SO = G.run_population(1)
+    Pall = np.concatenate([Pt, SO])
+    buf = dev(Pall)
+    G.local_search(buf[p:], buf[p:], p, 0, 2, 4 * G.nv, 7,
+                   plse.LS_PHASE1 | plse.LS_PHASE2 | plse.LS_REPAIR)
+    A = host(buf)
+    e = np.array([I.eval(A[k])[1] + G.nv * I.eval(A[k])[2] for k in range(2 * p)], dtype=np.int64)
+    sel_o, filled_o = I.pop_update(e, I.distances(A, A))
+    sel = empty((p,), torch.int32)
+    filled = empty((1,), torch.int32)
+    G.pop_update(p, buf, dev(e), sel, filled)
+    assert np.array_equal(host(sel), sel_o)
+    assert int(host(filled)[0]) == filled_o
+    G.close()

@@ -172,12 +172,17 @@ def test_aliasing_and_uneven_params(plse, oracle_mod):
         assert np.array_equal(S[w], So)
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4, 8])
+# (threads per walk, colouring placement: 1 shared memory, 2 global memory)
+LAUNCHES = [(16, 1), (16, 2), (32, 1), (32, 2), (64, 0), (128, 0), (256, 0)]
+
+
+@pytest.mark.parametrize("launch", LAUNCHES)
 @pytest.mark.parametrize("name", ["ri_n16_r06", "cyc_n33_r03", "cyc_n70_r06", "ri_n100_r08"])
-def test_warps_per_walk_do_not_change_results(plse, oracle_mod, name, warps):
+def test_launch_shape_does_not_change_results(plse, oracle_mod, name, launch):
     grid = cases()[name]
     G, I = plse.Instance(grid), oracle_mod.Instance(grid)
-    G.set_launch(warps)
+    lanes, place = launch
+    G.set_launch(lanes, 0, place)
     count = 12
     iters = min(2 * I.nv, 2500)
     P = I.init_population(count, 13)
@@ -185,7 +190,7 @@ def test_warps_per_walk_do_not_change_results(plse, oracle_mod, name, warps):
     S, f, F, st = run_gpu_ls(plse, G, P, 5, 9, iters, 31, flags)
     for w in range(count):
         So, Fo, sto = oracle_ls(I, P[w], 5 + w, 9, iters, 31, flags)
-        assert np.array_equal(S[w], So), (name, warps, w)
+        assert np.array_equal(S[w], So), (name, launch, w)
         assert F[w] == Fo and st[w].tolist() == [sto[k] for k in FIELDS]
     # PartialCol with the same launch shape
     S, f, F, st = run_gpu_ls(plse, G, P, 5, 9, iters, 31, plse.LS_REPAIR | plse.LS_PARTIALCOL)
