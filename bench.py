@@ -249,19 +249,29 @@ def run_gpu(args):
     for r, a, b in zip(RATIOS, after, before):
         mv = a["walks"]["moves"] - b["walks"]["moves"]
         it = a["walks"]["iterations"] - b["walks"]["iterations"]
-        per_inst.append({"r": r, "nv": insts[RATIOS.index(r)].nv, "moves": mv,
+        nvr = insts[RATIOS.index(r)].nv
+        budget = args.steps * args.pop * 12 * nvr        # phase 1 10|V| + phase 2 2|V| per walk
+        per_inst.append({"r": r, "nv": nvr, "moves": mv,
                          "ls_ms": round(a["ms_local_search"] - b["ms_local_search"], 2),
                          "cand_per_iter": round((a["walks"]["cand"] - b["walks"]["cand"]) / max(it, 1), 2),
+                         "iters_budget_use": round(it / budget, 4),
                          "best_score": a["score"]})
 
     ms_max, total_moves = reduce_over_ranks(ms, moves, "cuda")
     value = total_moves / (ms_max / 1e3)
 
-    # roofline of the dominant kernel (the local search), live from this run
+    # roofline of the dominant kernel (the local search), live from this run:
+    # the shared-memory peak is measured here by the library's own probe
+    # (conflict-free 16-byte loads on every SM), with the SM clock sampled
     peaks = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    smem_peak = sm_count * 128 * sm_max * 1e6 / 1e9          # GB/s
+    probe_clk = ClockSampler(dev)
+    probe_clk.start()
+    smem_bw = max(plse.smem_bandwidth(1 << 17)[0] for _ in range(3))
+    probe_clocks = probe_clk.stop()
+    smem_peak = smem_bw / 1e9                                  # GB/s
+    smem_derived = sm_count * 128 * sm_max * 1e6 / 1e9
     bytes_alg = walk_bytes(wdelta)
     launches_ls = len(insts) * args.steps
     achieved = bytes_alg / (ls_ms / 1e3) / 1e9 if ls_ms > 0 else None
@@ -274,8 +284,10 @@ def run_gpu(args):
                                  "launch with benchmark-length walks (%.1f B per move)" % LS_DRAM_BYTES_PER_MOVE
                                  if LS_DRAM_BYTES_PER_MOVE else "no capture of the current kernel"),
                 "kernel": "local_search_kernel",
-                "peak_source": "derived: %d SMs x 128 B/clk x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
-                               % (sm_count, sm_max),
+                "peak_source": ("measured: shared-memory load probe (plse_smem_bandwidth, 16-byte loads, 2 "
+                                "blocks of 1024 threads per SM), best of 3, SM clock %s MHz during the probe; "
+                                "derived bound %d SMs x 128 B/clk x %.0f MHz = %.1f GB/s"
+                                % (probe_clocks.get("sm_mhz"), sm_count, sm_max, smem_derived)),
                 "bytes_per_launch": round(bytes_alg / launches_ls),
                 "ms_per_launch": round(ls_ms / launches_ls, 3),
                 "moves_per_launch": round(wdelta["moves"] / launches_ls)}
@@ -291,7 +303,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, plse, inputs, seed)
     if rank == 0 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(sample_seconds=15.0)
+        out["cpu_baseline"] = cpu_baseline(sample_seconds=10.0)
     for G in insts:
         G.close()
     if world > 1:
@@ -328,21 +340,23 @@ def run_e2e(args, plse, inputs, seed):
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(budget_s=15.0):
+def oracle_sample(budget_s=15.0, chain=0):
     """The CPU oracle as it stands on a bounded sample of the workload, in the
     GA's steady state.  For each of the five instances two individuals A, B are
     brought to a steady state by an untimed generation of local search from
     random colourings.  Then, until that instance's share of the budget is
     spent: the AUX offspring of A with partner B (untimed, cheap) gets one timed
     generation of local search (phase 1 with 10|V| iterations, phase 2 with
-    2|V|, repair), and the pair becomes (B, result).  Single-threaded.
-    Returns (moves, seconds, description)."""
+    2|V|, repair), and the pair becomes (B, result).  Single-threaded; `chain`
+    offsets the individual indices (and so the trajectories) of independent
+    samples run side by side.  Returns (moves, seconds, generations)."""
     import numpy as np
     import oracle
     from paper_2103_10453_gb300 import inputs
     oracle.build()
     moves, secs, gens = 0, 0.0, 0
     share = budget_s / len(RATIOS)
+    base = 2 * chain
 
     def generation(I, S, ind, gen):
         S1, _, st1 = I.tabu_walk(S, ind, gen, 1, 10 * I.nv, 1)
@@ -352,59 +366,94 @@ def oracle_sample(budget_s=15.0):
 
     for r in RATIOS:
         I = oracle.Instance(inputs.n70(r))
-        P0 = I.init_population(2, 1)
-        A, _ = generation(I, P0[0], 0, 0)
-        B, _ = generation(I, P0[1], 1, 0)
+        P0 = I.init_population(base + 2, 1)
+        A, _ = generation(I, P0[base], base, 0)
+        B, _ = generation(I, P0[base + 1], base + 1, 0)
         t_inst, gen = 0.0, 1
         while t_inst < share:
             d = int(I.distances(A, B)[0, 0])
             if d == 0:                      # identical parents: restart B from random
-                B, _ = generation(I, I.init_population(1, 100 + gen)[0], 1, gen)
+                B, _ = generation(I, I.init_population(1, 100 + gen)[0], base + 1, gen)
                 gen += 1
                 continue
             pair = np.stack([A, B])
             O = I.crossover(pair, [1, 0], [[0, d], [d, 0]], gen, 1)[0]
             t0 = time.perf_counter()
-            S, m = generation(I, O, 0, gen)
+            S, m = generation(I, O, base, gen)
             t_inst += time.perf_counter() - t0
             moves += m
             A, B = B, S
             gen += 1
             gens += 1
         secs += t_inst
-    desc = ("%d steady-state generations of local search (phase 1 10|V| + phase 2 2|V| + repair) of "
-            "one AUX offspring each, spread over the five n=70 instances, single-threaded C oracle, "
-            "%.1f s timed" % (gens, secs))
-    return moves, secs, desc
+    return moves, secs, gens
 
 
-def cpu_baseline(sample_seconds=15.0):
-    moves, secs, desc = oracle_sample(sample_seconds)
-    return {"value": round(moves / secs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": desc, "seconds": round(secs, 2)}
+def _oracle_chain(args):
+    budget_s, chain = args
+    t0 = time.perf_counter()
+    moves, secs, gens = oracle_sample(budget_s, chain)
+    return moves, secs, gens, time.perf_counter() - t0
+
+
+def cpu_baseline(sample_seconds=15.0, cores=None):
+    """The oracle on the host: one single-threaded sample, then one independent
+    sample per core at once (walks are independent, so the all-core rate is the
+    sum of the chains' moves over the wall time of the slowest).  The pool uses
+    'spawn' so that no child inherits a CUDA context."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    m1, s1, g1 = oracle_sample(sample_seconds)
+    single = m1 / s1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_chain, [(sample_seconds, k + 1) for k in range(cores)])
+    wall = time.perf_counter() - t0
+    moves = sum(r[0] for r in res)
+    busy = max(r[3] for r in res)
+    value = moves / busy
+    desc = ("steady-state generations of local search (phase 1 10|V| + phase 2 2|V| + repair) of one "
+            "AUX offspring each, spread over the five n=70 instances; the C oracle single-threaded "
+            "(%d generations, %.1f s timed: %.4g moves/s), then %d independent chains at once on %d "
+            "host cores (%d generations, %.1f s wall)" % (g1, s1, single, cores, cores,
+                                                        sum(r[2] for r in res), busy))
+    return {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": desc, "seconds": round(wall, 2), "single_core_value": round(single, 1),
+            "host_cores": os.cpu_count()}
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    vals, total_m, total_s = [], 0, 0.0
-    desc = ""
-    for _ in range(args.warmup):
-        oracle_sample(2.0)
-    for _ in range(args.steps):
-        m, s, desc = oracle_sample(10.0)
-        vals.append(m / s)
-        total_m += m
-        total_s += s
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    vals, total_m, total_s, gens = [], 0, 0.0, 0
+    with ctx.Pool(cores) as pool:
+        for k in range(args.warmup + args.steps):
+            budget = 2.0 if k < args.warmup else 10.0
+            res = pool.map(_oracle_chain, [(budget, c + 1) for c in range(cores)])
+            if k < args.warmup:
+                continue
+            m = sum(r[0] for r in res)
+            s = max(r[3] for r in res)
+            vals.append(m / s)
+            total_m += m
+            total_s += s
+            gens += sum(r[2] for r in res)
     value = total_m / total_s
+    desc = ("%d steady-state generations of local search (phase 1 10|V| + phase 2 2|V| + repair) of one "
+            "AUX offspring each over the five n=70 instances, as %d independent single-threaded "
+            "chains of the C oracle at once on %d host cores, %d steps of 10 s" % (gens, cores, cores, args.steps))
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(1e3 * total_s / args.steps, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u8",
            "data": "synthetic (seeded instances of the paper's benchmark shapes)",
-           "config": workload_config(args.pop), "impl": "reference",
-           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "config": dict(workload_config(args.pop), parallelism="single"), "impl": "reference",
+           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": desc},
            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}

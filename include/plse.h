@@ -388,6 +388,14 @@ int  plse_matching(plse_handle h, int p, const uint8_t *P, const uint32_t *uid,
 int  plse_crossover(plse_handle h, int p, const uint8_t *P, const int32_t *partner,
                     const int32_t *dist, int gen, uint64_t seed, uint8_t *O, void *stream);
 
+/* ---- diagnostics -------------------------------------------------------------
+ * plse_smem_bandwidth -- measures the shared-memory load bandwidth of the
+ * current device (conflict-free 16-byte loads by two blocks of 1024 threads per
+ * SM, `iters` rounds of four loads per thread, timed by CUDA events); writes
+ * bytes/s (and the kernel's milliseconds, may be NULL).  The peak against which
+ * the local search's byte rate is reported; the paper has no counterpart. */
+int  plse_smem_bandwidth(int iters, double *bytes_per_s, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -251,6 +251,11 @@ size_t ls_workspace_bytes(const plse_instance *h, int slots)
            ws_align(4 * s) + ws_align(4 * 8);
 }
 
+int ensure_counters(plse_instance *h, cudaStream_t st)
+{
+    return grow(h, h->ws.counters, h->ws.counters_cap, 8, true, st);
+}
+
 int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
 {
     Workspace &ws = h->ws;

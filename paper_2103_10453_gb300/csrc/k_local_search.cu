@@ -531,56 +531,59 @@ __device__ __forceinline__ bool test_bit(const uint32_t (&m)[NWC], uint32_t k)
 
 // min over colours j in m of s_j (lowest j on ties) by most-significant-plane-
 // first elimination; returns -1 if m is empty
+// lowest set bit over the words (colour index), or -1; no branch
+template <int NWC>
+__device__ __forceinline__ int first_bit(const uint32_t (&set)[NWC])
+{
+    int jb = -1;
+#pragma unroll
+    for (int q = NWC - 1; q >= 0; --q) jb = set[q] ? q * 32 + __ffs(set[q]) - 1 : jb;
+    return jb;
+}
+
+// min over colours j in m of s_j (lowest j on ties) by most-significant-plane-
+// first elimination over the 8 planes of s, in straight-line code; planes 3..7
+// are skipped when no colour of the word set reaches 8; -1 if m is empty
 template <int NWC>
 __device__ __forceinline__ int bits_min(const uint32_t (&s)[NWC][8], const uint32_t (&m)[NWC], int &smin)
 {
-    uint32_t set[NWC], anym = 0, any0 = 0, any1 = 0, hi = 0, h1[NWC];
+    uint32_t set[NWC], hi = 0;
 #pragma unroll
     for (int q = 0; q < NWC; ++q) {
-        anym |= m[q];
-        h1[q] = s[q][1] | s[q][2] | s[q][3] | s[q][4] | s[q][5] | s[q][6] | s[q][7];
+        set[q] = m[q];
         hi |= s[q][3] | s[q][4] | s[q][5] | s[q][6] | s[q][7];
-        set[q] = m[q] & ~(s[q][0] | h1[q]);      // s_j = 0
-        any0 |= set[q];
     }
-    if (!anym) return -1;
-    if (any0) {
-        smin = 0;
-    } else {
+    uint32_t val = 0;
+    if (hi) {
+#pragma unroll
+        for (int p = 7; p >= 3; --p) {
+            uint32_t t[NWC], anyt = 0;
+#pragma unroll
+            for (int q = 0; q < NWC; ++q) {
+                t[q] = set[q] & ~s[q][p];
+                anyt |= t[q];
+            }
+            const bool keep = anyt != 0u;
+#pragma unroll
+            for (int q = 0; q < NWC; ++q) set[q] = keep ? t[q] : set[q];
+            val |= keep ? 0u : (1u << p);
+        }
+    }
+#pragma unroll
+    for (int p = 2; p >= 0; --p) {
+        uint32_t t[NWC], anyt = 0;
 #pragma unroll
         for (int q = 0; q < NWC; ++q) {
-            set[q] = m[q] & s[q][0] & ~h1[q];    // s_j = 1
-            any1 |= set[q];
+            t[q] = set[q] & ~s[q][p];
+            anyt |= t[q];
         }
-        if (any1) {
-            smin = 1;
-        } else {
-            uint32_t val = 0;
+        const bool keep = anyt != 0u;
 #pragma unroll
-            for (int q = 0; q < NWC; ++q) set[q] = m[q];
-#pragma unroll
-            for (int p = 7; p >= 0; --p) {
-                if (p > 2 && !hi) continue;
-                uint32_t t[NWC], anyt = 0;
-#pragma unroll
-                for (int q = 0; q < NWC; ++q) {
-                    t[q] = set[q] & ~s[q][p];
-                    anyt |= t[q];
-                }
-                if (anyt) {
-#pragma unroll
-                    for (int q = 0; q < NWC; ++q) set[q] = t[q];
-                } else {
-                    val |= 1u << p;
-                }
-            }
-            smin = (int)val;
-        }
+        for (int q = 0; q < NWC; ++q) set[q] = keep ? t[q] : set[q];
+        val |= keep ? 0u : (1u << p);
     }
-#pragma unroll
-    for (int q = 0; q < NWC; ++q)
-        if (set[q]) return q * 32 + __ffs(set[q]) - 1;
-    return -1;
+    smin = (int)val;
+    return first_bit<NWC>(set);
 }
 
 // Best admissible move of candidate v as key 2dF*256 + j (INT_MAX: none).
@@ -607,53 +610,91 @@ __device__ __forceinline__ int value3(const uint32_t (&s0)[NWC], const uint32_t 
     return (int)(((w0 >> b) & 1u) | (((w1 >> b) & 1u) << 1) | (((w2 >> b) & 1u) << 2));
 }
 
+// min over colours j in m of s_j = s0 + 2 s1 + 4 s2 (lowest j on ties) by a
+// most-significant-plane-first elimination, in straight-line code (selects, no
+// branches, so the lanes of a warp never split on the values); -1 if m is empty
 template <int NWC>
 __device__ __forceinline__ int bits_min3(const uint32_t (&s0)[NWC], const uint32_t (&s1)[NWC],
                                          const uint32_t (&s2)[NWC], const uint32_t (&m)[NWC], int &smin)
 {
-    uint32_t set[NWC], anym = 0, any0 = 0;
+    uint32_t set[NWC];
+    uint32_t val = 0;
 #pragma unroll
-    for (int q = 0; q < NWC; ++q) {
-        anym |= m[q];
-        set[q] = m[q] & ~(s0[q] | s1[q] | s2[q]);
-        any0 |= set[q];
-    }
-    if (!anym) return -1;
-    if (any0) {
-        smin = 0;
-    } else {
-        uint32_t val = 0;
+    for (int q = 0; q < NWC; ++q) set[q] = m[q];
 #pragma unroll
-        for (int q = 0; q < NWC; ++q) set[q] = m[q];
+    for (int p = 2; p >= 0; --p) {
+        uint32_t t[NWC], anyt = 0;
 #pragma unroll
-        for (int p = 2; p >= 0; --p) {
-            uint32_t t[NWC], anyt = 0;
-#pragma unroll
-            for (int q = 0; q < NWC; ++q) {
-                const uint32_t sp = p == 2 ? s2[q] : p == 1 ? s1[q] : s0[q];
-                t[q] = set[q] & ~sp;
-                anyt |= t[q];
-            }
-            if (anyt) {
-#pragma unroll
-                for (int q = 0; q < NWC; ++q) set[q] = t[q];
-            } else {
-                val |= 1u << p;
-            }
+        for (int q = 0; q < NWC; ++q) {
+            const uint32_t sp = p == 2 ? s2[q] : p == 1 ? s1[q] : s0[q];
+            t[q] = set[q] & ~sp;
+            anyt |= t[q];
         }
-        smin = (int)val;
-    }
+        const bool keep = anyt != 0u;              // some colour has bit p clear
 #pragma unroll
-    for (int q = 0; q < NWC; ++q)
-        if (set[q]) return q * 32 + __ffs(set[q]) - 1;
-    return -1;
+        for (int q = 0; q < NWC; ++q) set[q] = keep ? t[q] : set[q];
+        val |= keep ? 0u : (1u << p);
+    }
+    smin = (int)val;
+    return first_bit<NWC>(set);
 }
 
-// eval_vertex while all counts are <= 3: planes 0-1 of R and K only
+// The tabu rule of one candidate (Sec. 3.3).  The two cache entries of v are
+// authoritative for their colours; while an evicted entry of v may still be
+// live (emax >= t) any other colour is looked up in the global table G.  The
+// colours of m are taken in increasing (s_j, j) order, the order of their keys
+// 2dF*256 + j, and the first admissible one (not tabu, or aspirating: 2dF < A)
+// is the best move of m; a lookup in G is needed only for the colours that come
+// before it, usually none or one.
+struct TabuView {
+    uint32_t e0, e1, c0, c1;
+    bool gslow;                 // an evicted entry may be live: colours outside the cache go to G
+    uint32_t tabs;              // absolute clock of this iteration
+    const uint32_t *Gv;         // G row of v
+};
+
+__device__ __forceinline__ TabuView tabu_view(const DevInst &I, const uint2 &te, const Clock &ck, uint32_t trel,
+                                              const uint32_t *G, int v)
+{
+    TabuView t;
+    t.e0 = te.x & 0xFFFFu;
+    t.e1 = te.x >> 16;
+    t.c0 = te.y & 0xFFu;
+    t.c1 = (te.y >> 8) & 0xFFu;
+    t.gslow = (te.y >> 16) >= trel;
+    t.tabs = ck.base + ck.shift + trel;
+    t.Gv = G + (size_t)v * I.n1p;
+    return t;
+}
+
+// colour 0 (uncolouring v) and the cache colours still tabu (taken out of m,
+// admitted by aspiration only); returns the best key so far
+template <int NWC, typename SVAL>
+__device__ __forceinline__ int eval_special(const TabuView &tv, uint32_t trel, int i, int base2, int d2zero,
+                                            int mult, int A, uint32_t (&m)[NWC], SVAL sval)
+{
+    int best = INT_MAX;
+    if (i != 0) {
+        const bool tabu0 = tv.c0 == 0u ? tv.e0 >= trel : tv.c1 == 0u ? tv.e1 >= trel : (tv.gslow && tv.Gv[0] >= tv.tabs);
+        if (!tabu0 || d2zero < A) best = d2zero * kKeyScale;
+    }
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx) {
+        const uint32_t cs = sx ? tv.c1 : tv.c0, es = sx ? tv.e1 : tv.e0;
+        // an expired cache colour stays in m as an ordinary colour
+        if (cs != 0u && cs < 128u && es >= trel && test_bit<NWC>(m, cs)) {
+            clear_bit<NWC>(m, cs);
+            const int d2 = base2 + mult * sval(cs);
+            if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
+        }
+    }
+    return best;
+}
+
+// eval while all counts are <= 3: planes 0-1 of R and K only (sums <= 6)
 template <int NWC>
 __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, const uint32_t *G, const Clock &ck,
-                                               uint32_t trel, int v, int mult, int base_unc, int A, int &pairs,
-                                               bool &slow)
+                                               uint32_t trel, int v, int mult, int base_unc, int A, int &pairs)
 {
     // the tabu-cache entry (global memory) is loaded first and used last, so its
     // latency overlaps the shared-memory loads and the bit-sliced arithmetic
@@ -684,42 +725,32 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
         m[q] = ar4[q] & ac4[q];
         cnt += __popc(m[q]);
     }
-    pairs = cnt;
+    pairs = cnt;                                   // |D(v)| - 1 scanned moves
     if (i) clear_bit<NWC>(m, (uint32_t)i);
-    bool has0 = (i != 0);
-    int best = INT_MAX;
-    const uint32_t e0 = te.x & 0xFFFFu, e1 = te.x >> 16;
-    const uint32_t c0 = te.y & 0xFFu, c1 = (te.y >> 8) & 0xFFu, em = te.y >> 16;
-    slow = em >= trel;                        // evicted entries may apply: full evaluation
-    if (slow) return INT_MAX;
-#pragma unroll
-    // a cached colour whose tabu has expired is an ordinary admissible colour
-    // and stays in m; a still-tabu one is taken out and admitted by aspiration only
-    for (int sx = 0; sx < 2; ++sx) {
-        const uint32_t cs = sx ? c1 : c0, es = sx ? e1 : e0;
-        if (es < trel) continue;
-        if (cs == 0u) {
-            if (has0) {
-                has0 = false;
-                if (d2zero < A) best = min(best, d2zero * kKeyScale);
-            }
-        } else if (cs < 128u && test_bit<NWC>(m, cs)) {
-            clear_bit<NWC>(m, cs);
-            const int d2 = base2 + mult * value3<NWC>(s0, s1, s2, cs);
-            if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
+    const TabuView tv = tabu_view(I, te, ck, trel, G, v);
+    int best = eval_special<NWC>(tv, trel, i, base2, d2zero, mult, A, m,
+                                 [&](uint32_t k) { return value3<NWC>(s0, s1, s2, k); });
+    for (;;) {
+        int smin = 0;
+        const int jb = bits_min3<NWC>(s0, s1, s2, m, smin);
+        if (jb < 0) break;
+        const int d2 = base2 + mult * smin;
+        const bool tabu = tv.gslow && (uint32_t)jb != tv.c0 && (uint32_t)jb != tv.c1 && tv.Gv[jb] >= tv.tabs;
+        if (!tabu || d2 < A) {
+            best = min(best, d2 * kKeyScale + jb);
+            break;
         }
+        clear_bit<NWC>(m, (uint32_t)jb);
     }
-    if (has0) best = min(best, d2zero * kKeyScale);
-    int smin = 0;
-    const int jb = bits_min3<NWC>(s0, s1, s2, m, smin);
-    if (jb >= 0) best = min(best, (base2 + mult * smin) * kKeyScale + jb);
     return best;
 }
 
+// eval with exact counts (planes 2..6 read where a count reaches 4)
 template <int NWC>
 __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const uint32_t *G, const Clock &ck,
                                            uint32_t trel, int v, int mult, int base_unc, int A, int &pairs)
 {
+    const uint2 te = c.s.tc[v];
     const int i = c.s.S[v];
     const uint16_t rc = c.rc[v];
     const int r = rc >> 8, cc = rc & 255, rl = r, cl = I.n + cc;
@@ -764,52 +795,20 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
     }
     pairs = cnt;                                   // |D(v)| - 1 scanned moves
     if (i) clear_bit<NWC>(m, (uint32_t)i);
-    bool has0 = (i != 0);
-
-    const uint2 te = c.s.tc[v];
-    const uint32_t e0 = te.x & 0xFFFFu, e1 = te.x >> 16;
-    const uint32_t c0 = te.y & 0xFFu, c1 = (te.y >> 8) & 0xFFu, em = te.y >> 16;
-    int best = INT_MAX;
-    if (em < trel) {
-        // fast path: only the cached colours c0, c1 can be tabu
-#pragma unroll
-        for (int sx = 0; sx < 2; ++sx) {
-            const uint32_t cs = sx ? c1 : c0, es = sx ? e1 : e0;
-            if (es < trel) continue;                  // expired: stays in m
-            if (cs == 0u) {
-                if (has0) {
-                    has0 = false;
-                    if (d2zero < A) best = min(best, d2zero * kKeyScale);
-                }
-            } else if (cs < 128u && test_bit<NWC>(m, cs)) {
-                clear_bit<NWC>(m, cs);
-                const int d2 = base2 + mult * (count_of(c, rl, (int)cs) + count_of(c, cl, (int)cs));
-                if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
-            }
-        }
-        if (has0) best = min(best, d2zero * kKeyScale);
+    const TabuView tv = tabu_view(I, te, ck, trel, G, v);
+    int best = eval_special<NWC>(tv, trel, i, base2, d2zero, mult, A, m,
+                                 [&](uint32_t k) { return count_of(c, rl, (int)k) + count_of(c, cl, (int)k); });
+    for (;;) {
         int smin = 0;
         const int jb = bits_min<NWC>(s, m, smin);
-        if (jb >= 0) best = min(best, (base2 + mult * smin) * kKeyScale + jb);
-    } else {
-        // slow path: evicted entries of v may still be live, consult G
-        const uint32_t tabs = ck.base + ck.shift + trel;
-        const uint32_t *Gv = G + (size_t)v * I.n1p;
-        if (has0) {
-            const bool tabu = (c0 == 0u) ? (e0 >= trel) : (c1 == 0u) ? (e1 >= trel) : (Gv[0] >= tabs);
-            if (!tabu || d2zero < A) best = min(best, d2zero * kKeyScale);
+        if (jb < 0) break;
+        const int d2 = base2 + mult * smin;
+        const bool tabu = tv.gslow && (uint32_t)jb != tv.c0 && (uint32_t)jb != tv.c1 && tv.Gv[jb] >= tv.tabs;
+        if (!tabu || d2 < A) {
+            best = min(best, d2 * kKeyScale + jb);
+            break;
         }
-#pragma unroll
-        for (int q = 0; q < NWC; ++q) {
-            uint32_t bits = m[q];
-            while (bits) {
-                const uint32_t j = q * 32 + __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int d2 = base2 + mult * (count_of(c, rl, (int)j) + count_of(c, cl, (int)j));
-                const bool tabu = (j == c0) ? (e0 >= trel) : (j == c1) ? (e1 >= trel) : (Gv[j] >= tabs);
-                if (!tabu || d2 < A) best = min(best, d2 * kKeyScale + (int)j);
-            }
-        }
+        clear_bit<NWC>(m, (uint32_t)jb);
     }
     return best;
 }
@@ -977,10 +976,8 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         auto consider = [&](int v) {
             ++live;
             int pairs;
-            bool slow = true;
-            int kv = INT_MAX;
-            if (low) kv = eval_vertex_low<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs, slow);
-            if (slow) kv = eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs);
+            const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs)
+                               : eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs);
             st.pairs += pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, c.s.S[v]));
         };
@@ -1015,10 +1012,6 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         if (c.wg == 0) {
             const uint16_t rc = c.rc[v];
             const int r = rc >> 8, cc = rc & 255;
-            // count updates: lane 0 row r / colour i, lane 1 column cc / colour i,
-            // lanes 2-3 the same for colour j (folded into lanes 0-1 when i and j
-            // share a 32-colour word, so that no two lanes touch one plane word)
-            const bool same = i && j && ((i >> 5) == (j >> 5));
             // member-id XOR of (row r | column cc, colour i | j), read first so that
             // its latency overlaps the count updates: lane 0 row/i, 1 column/i,
             // 2 row/j, 3 column/j
@@ -1026,25 +1019,26 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             const int xline = (c.gl & 1) ? I.n + cc : r;
             const size_t xidx = (size_t)xline * I.n1p + xk;
             const int xold = (c.gl < 4 && xk) ? (int)c.s.xr[xidx] : 0;
+            // count updates: lane 0 on row r, lane 1 on column cc, colour i then j
+            // (one lane per line, so no two lanes touch one plane word)
             int cnt_i = 0, cnt_j = 0, dh = 0;
-            if (c.gl < 4) {
+            if (c.gl < 2) {
                 uint4 w;
-                if (c.gl < 2) {
-                    if (i) dh += count_step(c, xline, i, false, &w);
-                    if (same) dh += count_step(c, xline, j, true, &w);
-                    if (i) cnt_i = count_low(w, i);       // counts after the move (4 = four or more)
-                    if (same) cnt_j = count_low(w, j);
-                } else if (j && !same) {
+                if (i) {
+                    dh += count_step(c, xline, i, false, &w);
+                    cnt_i = count_low(w, i);              // counts after the move (4 = four or more)
+                }
+                if (j) {
                     dh += count_step(c, xline, j, true, &w);
                     cnt_j = count_low(w, j);
                 }
-                if (c.gl == 0) c.s.S[v] = (uint8_t)j;
-                if (xk) c.s.xr[xidx] = (uint16_t)(xold ^ v);   // v leaves i, joins j
             }
+            if (c.gl == 0) c.s.S[v] = (uint8_t)j;
+            if (c.gl < 4 && xk) c.s.xr[xidx] = (uint16_t)(xold ^ v);   // v leaves i, joins j
             const int dh_tot = __reduce_add_sync(c.gm, dh);
             // counts of colours i and j on the moved row and column, after the move
             const int Ri = __shfl_sync(c.gm, cnt_i, 0, W), Ki = __shfl_sync(c.gm, cnt_i, 1, W);
-            const int Rj = __shfl_sync(c.gm, cnt_j, same ? 0 : 2, W), Kj = __shfl_sync(c.gm, cnt_j, same ? 1 : 3, W);
+            const int Rj = __shfl_sync(c.gm, cnt_j, 0, W), Kj = __shfl_sync(c.gm, cnt_j, 1, W);
             __syncwarp(c.gm);
             // The mates whose conflict status can change, one per (line, colour) at
             // most: the only other holder of colour i (count after the move 1) and
@@ -1190,10 +1184,8 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         auto consider = [&](int v) {
             ++live;
             int pairs;
-            bool slow = true;
-            int kv = INT_MAX;
-            if (low) kv = eval_vertex_low<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs, slow);
-            if (slow) kv = eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs);
+            const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs)
+                               : eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs);
             st.pairs += pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, 0));
         };

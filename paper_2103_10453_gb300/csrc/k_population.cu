@@ -10,6 +10,7 @@
 // shared memory.  For the planes of a 2p population at n = 70 this is about
 // 3 KB per individual (L2-resident), against 2p^2 bytes of u16 matrices per
 // generation in HBM for the paper's stored-matrix design.
+#include <algorithm>
 #include <climits>
 
 #include "plse_pop.cuh"
@@ -215,15 +216,14 @@ __global__ void __launch_bounds__(256) chunk_local_kernel(const DevInst I, const
 // Sequential greedy over one chunk of sorted candidates (one warp).  Lane l
 // holds positions l, l+32, l+64, l+96 of the chunk with their current minimum
 // distance to the accepted set; the chunk's own distances are staged in shared
-// memory so each sequential step costs only shared loads and one shuffle.
-__global__ void __launch_bounds__(32) resolve_chunk_kernel(int chunk, int m, int p, int nv, int gamma,
-                                                           const int32_t *order, const int32_t *mind,
-                                                           const uint16_t *Dloc, int32_t *acc,
-                                                           int32_t *rej, SelState *s, const int *skip)
+// memory (Dc) so each sequential step costs only shared loads and one shuffle.
+// Values other blocks write during a persistent pass (mind, the state) are read
+// through L2 (ld.global.cg), never from a possibly stale L1 line.
+__device__ __forceinline__ void resolve_chunk(int chunk, int m, int p, int nv, int gamma, const int32_t *order,
+                                              const int32_t *mind, const uint16_t *Dloc, int32_t *acc,
+                                              int32_t *rej, SelState *s, uint16_t *Dc)
 {
-    if ((skip && *skip) || s->done) return;
-    __shared__ __align__(16) uint16_t Dc[kChunk * kChunk];
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int base = chunk * kChunk;
     const uint4 *src = reinterpret_cast<const uint4 *>(Dloc + (size_t)chunk * kChunk * kChunk);
     uint4 *dst = reinterpret_cast<uint4 *>(Dc);
@@ -232,11 +232,11 @@ __global__ void __launch_bounds__(32) resolve_chunk_kernel(int chunk, int m, int
 #pragma unroll
     for (int q = 0; q < kChunk / 32; ++q) {
         const int pos = base + lane + 32 * q;
-        md[q] = pos < m ? mind[pos] : INT_MAX;
+        md[q] = pos < m ? __ldcg(&mind[pos]) : INT_MAX;
         cd[q] = pos < m ? order[pos] : -1;
     }
     __syncwarp();
-    int nacc = s->nacc, nrej = s->nrej;
+    int nacc = __ldcg(&s->nacc), nrej = __ldcg(&s->nrej);
     if (lane == 0) s->chunk_acc_start = nacc;
     const int lim = min(kChunk, m - base);
     for (int qpos = 0; qpos < lim && nacc < p; ++qpos) {
@@ -267,20 +267,24 @@ __global__ void __launch_bounds__(32) resolve_chunk_kernel(int chunk, int m, int
     }
 }
 
-// min distance of every later candidate to the members accepted in `chunk`
-template <int NB>
-__global__ void __launch_bounds__(256) update_mind_kernel(const DevInst I, const uint32_t *planes,
-                                                          int chunk, int m, const int32_t *order,
-                                                          int32_t *mind, const int32_t *accl,
-                                                          const SelState *s, const int *skip)
+__global__ void __launch_bounds__(32) resolve_chunk_kernel(int chunk, int m, int p, int nv, int gamma,
+                                                           const int32_t *order, const int32_t *mind,
+                                                           const uint16_t *Dloc, int32_t *acc,
+                                                           int32_t *rej, SelState *s, const int *skip)
 {
     if ((skip && *skip) || s->done) return;
-    const int a0 = s->chunk_acc_start, a1 = s->nacc;
-    if (a1 <= a0) return;
-    __shared__ TileSmem<NB> sm;
-    __shared__ int ra[kTile], cb[kTile];
-    __shared__ int rowmin[kTile][17];
-    const int first = (chunk + 1) * kChunk + blockIdx.x * kTile;
+    __shared__ __align__(16) uint16_t Dc[kChunk * kChunk];
+    resolve_chunk(chunk, m, p, nv, gamma, order, mind, Dloc, acc, rej, s, Dc);
+}
+
+// min distance of the 64 candidates of tile `tb` after chunk `chunk` to the
+// members accepted in that chunk (acc[a0 .. a1)); every thread of the block
+template <int NB>
+__device__ __forceinline__ void update_mind_tile(const DevInst &I, const uint32_t *planes, int chunk, int tb, int m,
+                                                 const int32_t *order, int32_t *mind, const int32_t *accl, int a0,
+                                                 int a1, TileSmem<NB> &sm, int *ra, int *cb, int (*rowmin)[17])
+{
+    const int first = (chunk + 1) * kChunk + tb * kTile;
     if (first >= m) return;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     int best[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(256) update_mind_kernel(const DevInst I, const
         if (threadIdx.x < kTile) {
             const int pr = first + threadIdx.x, ac = c0 + threadIdx.x;
             ra[threadIdx.x] = pr < m ? order[pr] : -1;
-            cb[threadIdx.x] = ac < a1 ? accl[ac] : -1;
+            cb[threadIdx.x] = ac < a1 ? __ldcg(&accl[ac]) : -1;
         }
         __syncthreads();
         int acc[4][4];
@@ -307,15 +311,106 @@ __global__ void __launch_bounds__(256) update_mind_kernel(const DevInst I, const
         int v = INT_MAX;
         for (int q = 0; q < 16; ++q) v = min(v, rowmin[threadIdx.x][q]);
         const int pos = first + threadIdx.x;
-        if (pos < m) mind[pos] = min(mind[pos], v);
+        if (pos < m) mind[pos] = min(__ldcg(&mind[pos]), v);
+    }
+    __syncthreads();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) update_mind_kernel(const DevInst I, const uint32_t *planes,
+                                                          int chunk, int m, const int32_t *order,
+                                                          int32_t *mind, const int32_t *accl,
+                                                          const SelState *s, const int *skip)
+{
+    if ((skip && *skip) || s->done) return;
+    const int a0 = s->chunk_acc_start, a1 = s->nacc;
+    if (a1 <= a0) return;
+    __shared__ TileSmem<NB> sm;
+    __shared__ int ra[kTile], cb[kTile];
+    __shared__ int rowmin[kTile][17];
+    update_mind_tile<NB>(I, planes, chunk, blockIdx.x, m, order, mind, accl, a0, a1, sm, ra, cb, rowmin);
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident).  Thread 0
+// of each block arrives on a counter; the last one resets it and advances the
+// generation word the others wait on.  The wait is bounded: after kBarrierSpins
+// polls the block records the failure in err and leaves (false), so a broken
+// launch ends with an error instead of spinning forever.
+constexpr unsigned long long kBarrierSpins = 1ull << 24;
+
+__device__ __forceinline__ bool grid_sync(GridBar *b)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vg = &b->gen;
+        const unsigned g = *vg;
+        __threadfence();
+        ok = 1;
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vg == g) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(&b->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Alg. 4 over all chunks in one cooperative launch: block 0 resolves chunk k,
+// then every block updates the minimum distances of the later candidates to
+// the members just accepted, a grid barrier between the two.
+template <int NB>
+__global__ void __launch_bounds__(256) select_kernel(const DevInst I, const uint32_t *planes, int m, int p,
+                                                     int gamma, const int32_t *order, int32_t *mind,
+                                                     const uint16_t *Dloc, int32_t *acc, int32_t *rej,
+                                                     SelState *s, GridBar *bar, const int *skip)
+{
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) uint8_t dsm[];
+    TileSmem<NB> &sm = *reinterpret_cast<TileSmem<NB> *>(dsm);
+    uint16_t *Dc = reinterpret_cast<uint16_t *>(dsm + sizeof(TileSmem<NB>));
+    __shared__ int ra[kTile], cb[kTile];
+    __shared__ int rowmin[kTile][17];
+    volatile SelState *vs = s;
+    const int nchunks = (m + kChunk - 1) / kChunk;
+    for (int k = 0; k < nchunks; ++k) {
+        if (blockIdx.x == 0 && threadIdx.x < 32) resolve_chunk(k, m, p, I.nv, gamma, order, mind, Dloc, acc, rej, s, Dc);
+        if (!grid_sync(bar)) return;
+        if (vs->done) break;
+        const int a0 = vs->chunk_acc_start, a1 = vs->nacc;
+        const int rows = m - (k + 1) * kChunk;
+        if (a1 > a0 && rows > 0) {
+            const int tiles = (rows + kTile - 1) / kTile;
+            for (int tb = blockIdx.x; tb < tiles; tb += gridDim.x)
+                update_mind_tile<NB>(I, planes, k, tb, m, order, mind, acc, a0, a1, sm, ra, cb, rowmin);
+        }
+        if (!grid_sync(bar)) return;
     }
 }
 
 // fill rule and the final selection list
 __global__ void finish_selection_kernel(int p, const SelState *s, const int32_t *acc, const int32_t *rej,
-                                        int32_t *sel, int32_t *filled, const int *skip)
+                                        int32_t *sel, int32_t *filled, const GridBar *bar, int *error_flag,
+                                        const int *skip)
 {
     if (skip && *skip) return;
+    if (bar && bar->err) {                 // a barrier of the persistent pass gave up: the selection
+        for (int q = threadIdx.x; q < p; q += blockDim.x) sel[q] = q;   // stays valid, the error is reported
+        if (threadIdx.x == 0 && error_flag) atomicOr(error_flag, 2);
+        return;
+    }
     const int nacc = s->nacc;
     const int need = p - nacc;
     for (int q = threadIdx.x; q < p; q += blockDim.x)
@@ -506,25 +601,70 @@ cudaError_t launch_distance_matrix(const DevInst &I, const uint32_t *planesA, in
     return cudaGetLastError();
 }
 
+template <int NB>
+static cudaError_t launch_select(const DevInst &I, int m, int p, int gamma, const PopScratch &ps, const int *skip,
+                                 cudaStream_t st, bool *launched)
+{
+    *launched = false;
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop) return cudaSuccess;
+    const size_t dyn = sizeof(TileSmem<NB>) + sizeof(uint16_t) * kChunk * kChunk;
+    cudaError_t e = cudaFuncSetAttribute(select_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel<NB>, 256, dyn);
+    if (e != cudaSuccess || per_sm < 1) return e;
+    // as many blocks as there are 64-candidate tiles after the first chunk, at
+    // most the resident ones
+    const int tiles = std::max(1, (m - kChunk + kTile - 1) / kTile);
+    const int blocks = std::max(1, std::min(tiles, sms * per_sm));
+    const uint32_t *planes = ps.planes_ref;
+    int m_ = m, p_ = p, g_ = gamma;
+    DevInst I_ = I;
+    const int32_t *order = ps.order;
+    int32_t *mind = ps.mind, *acc = ps.acc, *rej = ps.rej;
+    const uint16_t *Dloc = ps.Dloc;
+    SelState *sst = ps.sel_state;
+    GridBar *bar = ps.bar;
+    const int *skp = skip;
+    void *args[] = {&I_, &planes, &m_, &p_, &g_, &order, &mind, &Dloc, &acc, &rej, &sst, &bar, &skp};
+    e = cudaLaunchCooperativeKernel((const void *)select_kernel<NB>, dim3(blocks), dim3(256), args, dyn, st);
+    if (e == cudaSuccess) *launched = true;
+    return e;
+}
+
 cudaError_t launch_pop_update(const DevInst &I, int p, const uint32_t *planes, const int64_t *e,
-                              int gamma, const PopScratch &ps, int32_t *sel, int32_t *filled,
-                              const int *skip, cudaStream_t st)
+                              int gamma, const PopScratch &ps_in, int32_t *sel, int32_t *filled,
+                              const int *skip, cudaStream_t st, long long *kernels)
 {
     const int m = 2 * p;
+    PopScratch ps = ps_in;
+    ps.planes_ref = planes;
     cudaError_t err = cudaMemsetAsync(ps.sel_state, 0, sizeof(SelState), st);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(ps.bar, 0, sizeof(GridBar), st);
     if (err != cudaSuccess) return err;
     rank_kernel<<<grid_for(m, 256), 256, 0, st>>>(e, m, ps.order, skip);
     fill_int_kernel<<<grid_for(m, 256), 256, 0, st>>>(ps.mind, m, INT_MAX, skip);
     const int nchunks = (m + kChunk - 1) / kChunk;
     NB_DISPATCH(I.nb, (chunk_local_kernel<NBV><<<dim3(nchunks, 4), 256, 0, st>>>(I, planes, ps.order, m, ps.Dloc, skip)));
-    for (int k = 0; k < nchunks; ++k) {
-        resolve_chunk_kernel<<<1, 32, 0, st>>>(k, m, p, I.nv, gamma, ps.order, ps.mind, ps.Dloc, ps.acc,
-                                               ps.rej, ps.sel_state, skip);
-        const int rows = m - (k + 1) * kChunk;
-        if (rows > 0)
-            NB_DISPATCH(I.nb, (update_mind_kernel<NBV><<<(rows + kTile - 1) / kTile, 256, 0, st>>>(I, planes, k, m, ps.order, ps.mind, ps.acc, ps.sel_state, skip)));
+    bool launched = false;
+    NB_DISPATCH(I.nb, (err = launch_select<NBV>(I, m, p, gamma, ps, skip, st, &launched)));
+    if (err != cudaSuccess) return err;
+    if (kernels) *kernels = launched ? 5 : 4 + nchunks + (nchunks - 1);
+    if (!launched) {                       // no cooperative launch: one kernel pair per chunk
+        for (int k = 0; k < nchunks; ++k) {
+            resolve_chunk_kernel<<<1, 32, 0, st>>>(k, m, p, I.nv, gamma, ps.order, ps.mind, ps.Dloc, ps.acc,
+                                                   ps.rej, ps.sel_state, skip);
+            const int rows = m - (k + 1) * kChunk;
+            if (rows > 0)
+                NB_DISPATCH(I.nb, (update_mind_kernel<NBV><<<(rows + kTile - 1) / kTile, 256, 0, st>>>(I, planes, k, m, ps.order, ps.mind, ps.acc, ps.sel_state, skip)));
+        }
     }
-    finish_selection_kernel<<<1, 256, 0, st>>>(p, ps.sel_state, ps.acc, ps.rej, sel, filled, skip);
+    finish_selection_kernel<<<1, 256, 0, st>>>(p, ps.sel_state, ps.acc, ps.rej, sel, filled, ps.bar,
+                                               ps.error_flag, skip);
     return cudaGetLastError();
 }
 

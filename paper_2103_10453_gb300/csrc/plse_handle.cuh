@@ -90,6 +90,8 @@ uint32_t tenure_reciprocal(int alpha_num, int alpha_den, int nv);
 LSArgs ls_args(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0, int gen, int64_t iters,
                uint64_t seed, int flags, int32_t *f_out, int64_t *F_out, plse_walk_stats *stats, const int *skip);
 int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st);
+// the walk counter and the device check flag (read by plse_sync), allocated once
+int ensure_counters(plse_instance *h, cudaStream_t st);
 int enqueue_local_search(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0,
                          int gen, int64_t iters, uint64_t seed, int flags, int32_t *f_out,
                          int64_t *F_out, plse_walk_stats *stats, cudaStream_t st,

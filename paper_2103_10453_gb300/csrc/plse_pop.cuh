@@ -15,6 +15,14 @@ struct SelState {
     int chunk_acc_start;  // nacc when the current chunk started
 };
 
+// barrier words of a cooperative (persistent) Alg. 4 pass
+struct GridBar {
+    unsigned count;       // blocks arrived at the current barrier
+    unsigned gen;         // barriers completed
+    int err;              // nonzero: a block gave up waiting
+    int pad;
+};
+
 // device scratch of Alg. 4 for populations of up to `cap_p`
 struct PopScratch {
     int cap_p = 0;
@@ -24,6 +32,9 @@ struct PopScratch {
     int32_t *rej = nullptr;    // [2p] rejected candidates in rank order
     uint16_t *Dloc = nullptr;  // [chunks][kChunk][kChunk] chunk-local distances
     SelState *sel_state = nullptr;
+    GridBar *bar = nullptr;
+    const uint32_t *planes_ref = nullptr;  // set by launch_pop_update for its kernels
+    int *error_flag = nullptr;             // set by the caller: a failed pass is reported here
 };
 
 cudaError_t launch_planes(const DevInst &I, const uint8_t *P, int count, uint32_t *planes, cudaStream_t st);
@@ -31,7 +42,8 @@ cudaError_t launch_distance_matrix(const DevInst &I, const uint32_t *planesA, in
                                    const uint32_t *planesB, int nb, int32_t *D, cudaStream_t st);
 cudaError_t launch_pop_update(const DevInst &I, int p, const uint32_t *planes, const int64_t *e,
                               int gamma, const PopScratch &ps, int32_t *sel, int32_t *filled,
-                              const int *skip, cudaStream_t st);
+                              const int *skip, cudaStream_t st,
+                              long long *kernels = nullptr);
 cudaError_t launch_matching(const DevInst &I, int p, const uint32_t *planes, const uint32_t *uid,
                             uint32_t *tested, int32_t *tcount, int cap, int random, int gen,
                             uint64_t seed, int32_t *partner, int32_t *dist, const int *skip,

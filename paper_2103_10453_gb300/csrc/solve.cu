@@ -236,7 +236,7 @@ int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p, cudaStream_t st)
     int rc;
     if ((rc = dalloc(h, ps.order, m, st)) || (rc = dalloc(h, ps.mind, m, st)) || (rc = dalloc(h, ps.acc, p, st)) ||
         (rc = dalloc(h, ps.rej, m, st)) || (rc = dalloc(h, ps.Dloc, (size_t)nchunks * kChunk * kChunk, st)) ||
-        (rc = dalloc(h, ps.sel_state, 1, st)))
+        (rc = dalloc(h, ps.sel_state, 1, st)) || (rc = dalloc(h, ps.bar, 1, st)))
         return rc;
     ps.cap_p = p;
     return PLSE_OK;
@@ -245,7 +245,7 @@ int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p, cudaStream_t st)
 void free_pop_scratch(plse_instance *h, PopScratch &ps, cudaStream_t st)
 {
     h_free(h, ps.order, st); h_free(h, ps.mind, st); h_free(h, ps.acc, st); h_free(h, ps.rej, st);
-    h_free(h, ps.Dloc, st); h_free(h, ps.sel_state, st);
+    h_free(h, ps.Dloc, st); h_free(h, ps.sel_state, st); h_free(h, ps.bar, st);
     ps = PopScratch();
 }
 
@@ -275,7 +275,7 @@ size_t solver_bytes(const plse_instance *h, int p, int gens)
          a((size_t)I.nv) + a(4 * (size_t)gens);
     const int m = 2 * p, nchunks = (m + kChunk - 1) / kChunk;
     t += a(4 * (size_t)m) + a(4 * (size_t)m) + a(4 * (size_t)p) + a(4 * (size_t)m) +
-         a(2 * (size_t)nchunks * kChunk * kChunk) + a(sizeof(SelState));
+         a(2 * (size_t)nchunks * kChunk * kChunk) + a(sizeof(SelState)) + a(sizeof(GridBar));
     return t;
 }
 
@@ -325,13 +325,6 @@ static int ensure_solver(plse_instance *h, int p, int gens, cudaStream_t st)
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);       \
     } while (0)
-
-// kernel launches of one plse_pop_update pass over 2p candidates
-static long long pop_update_launches(int p)
-{
-    const int nchunks = (2 * p + kChunk - 1) / kChunk;
-    return 4 + nchunks + (nchunks - 1);
-}
 
 int run_begin(plse_instance *h, int pop, int max_generations, int64_t iters, uint64_t seed, cudaStream_t st)
 {
@@ -438,7 +431,10 @@ static int issue_generation_rest(plse_instance *h, const GenPlan &q)
     CK(cudaMemcpyAsync(s->hflag + 2 * q.slot, s->ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(s->gev[q.slot][2], st));
     CK(launch_planes(I, q.Pp, p, s->planes[cur] + (size_t)p * stride, st));
-    CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st));
+    s->ps.error_flag = h->ws.counters ? h->ws.counters + 1 : nullptr;
+    long long sel_kernels = 0;
+    CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st,
+                         &sel_kernels));
     gather_kernel<<<(p * 32 + 255) / 256, 256, 0, st>>>(
         I, p, g, s->sel, s->Pall[cur], s->planes[cur], s->e[cur], s->uid[cur], s->tested[cur], s->tcount[cur],
         cap, s->Pall[nxt], s->planes[nxt], s->e[nxt], s->uid[nxt], s->tested[nxt], s->tcount[nxt], skip);
@@ -447,7 +443,7 @@ static int issue_generation_rest(plse_instance *h, const GenPlan &q)
                        prm.matching == PLSE_MATCH_RANDOM, g, se.seed, s->partner, s->dist, skip, st));
     CK(launch_crossover(I, p, s->Pall[nxt], s->partner, s->dist, g, se.seed, prm.beta,
                         prm.crossover == PLSE_XOVER_UX, s->SO, skip, st));
-    se.launches += 3 + pop_update_launches(p) + 3;
+    se.launches += 3 + sel_kernels + 3;
     se.cur = nxt;
     se.issued = g + 1;
     return PLSE_OK;
@@ -743,6 +739,8 @@ int plse_pop_update(plse_handle h, int p, const uint8_t *Pall, const int64_t *e,
     int rc = ensure_step_planes(h, 2 * (size_t)p, st);
     if (rc) return rc;
     if ((rc = ensure_pop_scratch(h, h->step_ps, p, st))) return rc;
+    if ((rc = ensure_counters(h, st))) return rc;
+    h->step_ps.error_flag = h->ws.counters + 1;
     if (h->nv > 0) CK(launch_planes(h->di, Pall, 2 * p, h->step_planes, st));
     CK(launch_pop_update(h->di, p, h->step_planes, e, h->params.spacing_gamma, h->step_ps, sel, filled,
                          nullptr, st));

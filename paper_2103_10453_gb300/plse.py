@@ -84,6 +84,7 @@ SIGNATURES = {
     "plse_last_error_detail": (C.c_int, [_vp, C.c_char_p, C.c_size_t]),
     "plse_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "plse_sync": (C.c_int, [_vp, _vp]),
+    "plse_smem_bandwidth": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "plse_autotune": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "plse_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
@@ -353,6 +354,17 @@ class Instance:
 
 def _job(pop, generations, iters, seed):
     return Job(int(pop), int(generations), int(iters), int(seed))
+
+
+def smem_bandwidth(iters=4096):
+    """Measured shared-memory load bandwidth of the current device in bytes/s
+    (plse_smem_bandwidth) and the probe's milliseconds."""
+    lib = load()
+    bw, ms = C.c_double(), C.c_double()
+    rc = lib.plse_smem_bandwidth(int(iters), C.byref(bw), C.byref(ms))
+    if rc != PLSE_OK:
+        raise PlseError(rc, "plse_smem_bandwidth")
+    return bw.value, ms.value
 
 
 def solve_batch(instances, jobs, max_inflight=0):
