@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="batching case instead of the benchmark: 64 uneven instances solved one "
                          "by one with plse_solve, then together with plse_solve_batch")
-    ap.add_argument("--batch-pop", type=int, default=1024)
+    ap.add_argument("--batch-set", default="both", choices=["mix", "multistart", "both"])
+    ap.add_argument("--batch-pop", type=int, default=0,
+                    help="with --batch: one population for every job (default: by the size rule)")
     ap.add_argument("--generations", type=int, default=10,
                     help="generations per job of --batch and --serve")
     ap.add_argument("--inflight", type=int, default=None,
@@ -75,8 +77,8 @@ def parse():
     ap.add_argument("--serve-walks", type=int, default=4,
                     help="with --serve: cap on local-search walks per block (0 = automatic); a "
                          "low cap leaves each SM room for other requests' short kernels")
-    ap.add_argument("--serve-compare", action="store_true",
-                    help="with --serve: also run the same jobs at once through plse_solve_batch")
+    ap.add_argument("--serve-mem", type=float, default=1.0,
+                    help="with --serve: device-memory budget of the server in GB")
     ap.add_argument("--rate", type=float, default=20.0)
     return ap.parse_args()
 
@@ -497,108 +499,182 @@ def run_ls_case(args):
     G.close()
 
 
+def batch_pop(nv, cells=1 << 22):
+    """Population of a batched job, fixed by its size (never by load): the
+    largest power of two p with p*|V| <= 4M colour cells (about 4 MB per copy
+    of the population), within [1024, 16384]."""
+    p = 1024
+    while p * 2 <= 16384 and p * 2 * nv <= cells:
+        p *= 2
+    return p
+
+
 def run_batch_case(args):
-    """64 uneven instances (n in {20..70}, r ~ U[0.3, 0.8], cyclic-delete or
-    random insertion by a coin, seeds 4000+k), population --batch-pop,
+    """Batching.  Two job sets:
+      mix        -- 64 uneven instances (n in {20..70}, r ~ U[0.3, 0.8],
+                    cyclic-delete or random insertion by a coin, seeds 4000+k),
+                    population by the size rule of batch_pop (--batch-pop
+                    overrides it);
+      multistart -- 16 runs of the n = 70, r = 0.5 instance with seeds 1..16,
+                    population 1024;
     --generations generations, phase-1 iterations 10|V|, optimality stop on.
-    Wall clock of 64 sequential plse_solve calls against one plse_solve_batch
-    call; every job's score, grid and walk counters must be identical."""
+    Each set runs as sequential plse_solve calls, as one plse_solve_batch call
+    with 16 concurrent runs (each run on its own stream), and as one
+    plse_solve_batch call in lockstep mode (every generation's local searches
+    in one persistent multi-instance launch per colour-word class); every job's
+    score, grid and walk counters must be identical across the three."""
     import numpy as np
     import torch
     from paper_2103_10453_gb300 import inputs, plse
-    grids = inputs.batch_mix(64)
-    insts = [plse.Instance(g) for g in grids]
-    jobs = [(args.batch_pop, args.generations, 10 * G.nv, 1) for G in insts]
-    insts[0].solve(*jobs[0])                       # warm-up: module load, first allocations
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    seq = [G.solve(*j, with_stats=True) for G, j in zip(insts, jobs)]
-    t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    inflight = args.inflight or 16
-    bat, rc = plse.solve_batch(insts, jobs, max_inflight=inflight)
-    t_bat = time.perf_counter() - t0
-    same = rc == 0 and all(a["score"] == b["score"] and np.array_equal(a["best_grid"], b["best_grid"])
-                           and a["walks"] == b["walks"] for a, b in zip(seq, bat))
-    moves = sum(r["walks"]["moves"] for r in bat)
-    print(json.dumps({"case": "batch", "jobs": len(jobs), "population": args.batch_pop,
-                      "generations": args.generations, "max_inflight": inflight,
-                      "sequential_s": round(t_seq, 3), "batched_s": round(t_bat, 3),
-                      "speedup": round(t_seq / t_bat, 3), "identical": bool(same),
-                      "moves": moves, "batched_moves_per_s": round(moves / t_bat, 1),
-                      "sequential_moves_per_s": round(moves / t_seq, 1),
-                      "solved_to_bound": sum(1 for G, r in zip(insts, bat) if r["score"] == G.ub)}),
-          flush=True)
-    for G in insts:
-        G.close()
+
+    def run_set(name, grids, jobs):
+        warm = plse.Instance(grids[0])
+        warm.solve(*jobs[0])
+        warm.close()
+        torch.cuda.synchronize()
+        out = {"jobs": len(jobs), "generations": args.generations, "phase1_iters": "10|V|"}
+        pops = [j[0] for j in jobs]
+        out["population"] = {"min": min(pops), "max": max(pops), "sum": sum(pops)}
+        insts = [plse.Instance(g) for g in grids]
+        t0 = time.perf_counter()
+        seq = [G.solve(*j, with_stats=True) for G, j in zip(insts, jobs)]
+        t_seq = time.perf_counter() - t0
+        for G in insts:
+            G.close()
+        moves = sum(r["walks"]["moves"] for r in seq)
+        out["sequential"] = {"s": round(t_seq, 3), "solves_per_s": round(len(jobs) / t_seq, 3),
+                             "moves_per_s": round(moves / t_seq, 1)}
+        for mode, inflight in (("concurrent", 16), ("lockstep", 0)):
+            binsts = [plse.Instance(g) for g in grids]
+            t0 = time.perf_counter()
+            bat, rc = plse.solve_batch(binsts, jobs, max_inflight=inflight, lockstep=(mode == "lockstep"))
+            t_b = time.perf_counter() - t0
+            same = rc == 0 and all(a["score"] == b["score"] and np.array_equal(a["best_grid"], b["best_grid"])
+                                   and a["walks"] == b["walks"] for a, b in zip(seq, bat))
+            out[mode] = {"s": round(t_b, 3), "solves_per_s": round(len(jobs) / t_b, 3),
+                         "moves_per_s": round(moves / t_b, 1), "speedup": round(t_seq / t_b, 3),
+                         "identical": bool(same)}
+            for G in binsts:
+                G.close()
+        out["solved_to_bound"] = sum(1 for g, r in zip(grids, seq) if r["score"] == plse.Instance(g).ub)
+        return out
+
+    res = {"case": "batch"}
+    if args.batch_set in ("mix", "both"):
+        grids = inputs.batch_mix(64)
+        nvs = [plse.Instance(g).nv for g in grids]
+        jobs = [(args.batch_pop or batch_pop(nv), args.generations, 10 * nv, 1) for nv in nvs]
+        res["mix"] = run_set("mix", grids, jobs)
+        res["mix"]["population_rule"] = ("largest power of two with p*|V| <= 2^22, in [1024, 16384]"
+                                         if not args.batch_pop else "fixed")
+    if args.batch_set in ("multistart", "both"):
+        g = inputs.n70(0.5)
+        nv = plse.Instance(g).nv
+        grids = [g] * 16
+        jobs = [(1024, args.generations, 10 * nv, 1 + k) for k in range(16)]
+        res["multistart"] = run_set("multistart", grids, jobs)
+    print(json.dumps(res), flush=True)
 
 
 def run_serve_case(args):
-    """--requests requests with Poisson arrivals at --rate per second into one
-    plse_server (max_inflight --inflight): a quarter LSC-style cyclic-delete
-    requests with n in [60, 100], the rest random insertion with n uniform over
-    {10..100}, r ~ U[0.3, 0.8], seeds 5000+k; --generations generations with the
-    optimality stop, phase-1 iterations 10 x empty cells, population by size.
-    Reports time-to-result percentiles (arrival to completion) and solves/s."""
+    """Serving: --requests requests of the serving mix (a quarter LSC-style
+    cyclic-delete requests with n in [60, 100], the rest random insertion with n
+    uniform over {10..100}, r ~ U[0.3, 0.8], seeds 5000+k), --generations
+    generations each with the optimality stop, phase-1 iterations 10 x empty
+    cells, population by size (never by load).  Three measurements:
+      sequential  -- the same requests through plse_solve one after another;
+      capacity    -- all requests submitted at once to one plse_server (closed
+                     loop): the sustainable solves/s;
+      open loop   -- Poisson arrivals at min(--rate, 0.8 x capacity) into a fresh
+                     server: time to result (arrival to completion) p50/p90/p99.
+    The servers admit by device memory (--serve-mem GB) and by --inflight run
+    slots; every served result must equal plse_solve of the same request."""
     import numpy as np
     from paper_2103_10453_gb300 import inputs, plse
     grids = inputs.serve_mix(args.requests)
-    arrivals = inputs.poisson_arrivals(args.requests, args.rate)
+    jobs = [(inputs.serve_pop(g), args.generations, 10 * int((g == 0).sum()), 1) for g in grids]
     inflight = args.inflight or 64
-    srv = plse.Server(max_inflight=inflight, max_queue=args.requests)
-    srv.set_launch(0, args.serve_walks)
-    # warm-up request (module load, first allocations), not counted
-    w = srv.submit(inputs.tiny_n10(), 32, 2, 100, 1)
-    srv.poll(w, wait_ms=-1)
+    budget = int(args.serve_mem * (1 << 30))
+
+    def same(a, b):
+        return a["score"] == b["score"] and np.array_equal(a["best_grid"], b["best_grid"]) and \
+            a["walks"] == b["walks"]
+
+    def new_server():
+        srv = plse.Server(max_inflight=inflight, max_queue=args.requests + 8, mem_budget=budget)
+        srv.set_launch(0, args.serve_walks)
+        w = srv.submit(inputs.tiny_n10(), 32, 2, 100, 1)       # warm-up, not counted
+        srv.poll(w, wait_ms=-1)
+        return srv
+
+    # sequential plse_solve
+    G = plse.Instance(inputs.tiny_n10())
+    G.solve(32, 2, 100, 1)
+    G.close()
+    t0 = time.perf_counter()
+    seq = []
+    for g, j in zip(grids, jobs):
+        H = plse.Instance(g)
+        seq.append(H.solve(*j, with_stats=True))
+        H.close()
+    t_seq = time.perf_counter() - t0
+
+    # capacity: closed loop
+    srv = new_server()
+    t0 = time.perf_counter()
+    tickets = [srv.submit(g, *j) for g, j in zip(grids, jobs)]
+    cap_res = [srv.poll(t, wait_ms=-1) for t in tickets]
+    t_cap = time.perf_counter() - t0
+    cap_mem = srv.memory()
+    srv.close()
+    capacity = len(grids) / t_cap
+
+    # open loop at a sustainable rate
+    rate = min(args.rate, 0.8 * capacity)
+    arrivals = inputs.poisson_arrivals(args.requests, rate)
+    srv = new_server()
     tickets = []
     t0 = time.perf_counter()
-    for g, ta in zip(grids, arrivals):
+    for (g, j), ta in zip(zip(grids, jobs), arrivals):
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
-        empty = int((g == 0).sum())
-        tickets.append(srv.submit(g, inputs.serve_pop(g), args.generations, 10 * empty, 1))
+        tickets.append(srv.submit(g, *j))
     res = [srv.poll(t, wait_ms=-1) for t in tickets]
     t_all = time.perf_counter() - t0
+    mem = srv.memory()
     srv.close()
     lat = np.array([r["ms_wall"] for r in res])
-    run_ms = np.array([r["ms_wall"] - r["ms_queue"] for r in res])
-    dev_ms = np.array([r["ms_total"] for r in res])
+    qms = np.array([r["ms_queue"] for r in res])
     ok = sum(1 for r in res if r["status"] == 0)
-    compare = None
-    if args.serve_compare:
-        # the same jobs with every request present at once, through plse_solve_batch
-        insts = [plse.Instance(g) for g in grids]
-        jobs = [(inputs.serve_pop(g), args.generations, 10 * int((g == 0).sum()), 1) for g in grids]
-        t1 = time.perf_counter()
-        bat, rc = plse.solve_batch(insts, jobs, max_inflight=inflight)
-        compare = {"batch_wall_s": round(time.perf_counter() - t1, 3), "rc": rc,
-                   "identical": all(a["score"] == b["score"] and a["walks"] == b["walks"]
-                                    for a, b in zip(res, bat))}
-        for G in insts:
-            G.close()
     errors = {}
     for g, r in zip(grids, res):
         if r["status"] != 0:
             key = "%d: %s" % (r["status"], r["detail"][:80])
             errors.setdefault(key, []).append(int(g.shape[0]))
-    print(json.dumps({"case": "serve", "requests": args.requests, "rate_per_s": args.rate,
-                      "max_inflight": inflight, "walks_per_block_cap": args.serve_walks, "generations": args.generations,
-                      "ok": ok, "wall_s": round(t_all, 3), "solves_per_s": round(ok / t_all, 3),
+    print(json.dumps({
+        "case": "serve", "requests": args.requests, "generations": args.generations,
+        "phase1_iters": "10 x empty cells", "population": "2^16 / empty cells, power of two in [32, 512]",
+        "max_inflight": inflight, "mem_budget_bytes": budget,
+        "sequential": {"wall_s": round(t_seq, 3), "solves_per_s": round(len(grids) / t_seq, 3)},
+        "capacity": {"wall_s": round(t_cap, 3), "solves_per_s": round(capacity, 3),
+                     "vs_sequential": round(t_seq / t_cap, 3),
+                     "identical_to_sequential": all(same(a, b) for a, b in zip(cap_res, seq)),
+                     "memory": cap_mem},
+        "open_loop": {"rate_per_s": round(rate, 3), "requested_rate_per_s": args.rate, "ok": ok,
+                      "wall_s": round(t_all, 3), "solves_per_s": round(ok / t_all, 3),
                       "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
                                      "p90": round(float(np.percentile(lat, 90)), 1),
                                      "p99": round(float(np.percentile(lat, 99)), 1),
                                      "max": round(float(lat.max()), 1)},
-                      "queue_ms_p50": round(float(np.percentile([r["ms_queue"] for r in res], 50)), 1),
-                      "run_ms": {"p50": round(float(np.percentile(run_ms, 50)), 1),
-                                 "p90": round(float(np.percentile(run_ms, 90)), 1)},
-                      "device_ms": {"p50": round(float(np.percentile(dev_ms, 50)), 1),
-                                    "p90": round(float(np.percentile(dev_ms, 90)), 1)},
-                      "generations_mean": round(float(np.mean([r["generations"] for r in res])), 2),
-                      "same_jobs_as_one_batch": compare,
-                      "moves": sum(r["walks"]["moves"] for r in res),
-                      "errors": {k: {"count": len(v), "n": sorted(set(v))[:10]} for k, v in errors.items()}}),
-          flush=True)
+                      "queue_ms": {"p50": round(float(np.percentile(qms, 50)), 1),
+                                   "p99": round(float(np.percentile(qms, 99)), 1)},
+                      "identical_to_sequential": all(same(a, b) for a, b in zip(res, seq)),
+                      "memory": mem},
+        "generations_mean": round(float(np.mean([r["generations"] for r in res])), 2),
+        "moves": sum(r["walks"]["moves"] for r in res),
+        "errors": {k: {"count": len(v), "n": sorted(set(v))[:10]} for k, v in errors.items()}}),
+        flush=True)
 
 
 def run_pop_sweep(args):

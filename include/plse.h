@@ -242,20 +242,28 @@ typedef struct {
 } plse_result;
 
 /* plse_solve_batch -- runs job i on handle hs[i] (with that handle's
- * parameters).  With max_inflight = 0 and a handle of its own for every job,
- * all runs advance one generation at a time and the local searches of a
- * generation run as one persistent launch per colour-word class (orders n
- * below 32, 64, 96, 128), which takes the runs' walks in turn so that one run's
- * tail is filled with the next run's walks; the rest of each generation runs on
- * the run's own stream; a class whose first handle has automatic launch knobs
- * gets them from plse_autotune on its largest instance.  Otherwise up to
- * `max_inflight` jobs run at a time
- * (0 = 16), each on its own stream, with their kernels overlapping on the
- * current device, and jobs naming the same handle run one after another.  best_grids (may be NULL, entries may be
- * NULL): host int8 [n_i*n_i] outputs as plse_solve.  results: host [count].
- * Every job's result equals that of plse_solve with the same arguments.
- * Blocks until every job is done; returns the first job error (in index order)
- * or PLSE_OK; results[i].status holds each job's own code. */
+ * parameters).  Two ways to share the device:
+ *   concurrent: up to `max_inflight` runs at a time (0 = 16), each on its own
+ *     stream, each advancing at its own pace, their kernels overlapping on the
+ *     current device; jobs naming the same handle run one after another;
+ *   lockstep (max_inflight = PLSE_BATCH_LOCKSTEP, a handle per job): all runs
+ *     advance one generation at a time, and the local searches of a generation
+ *     run as one persistent launch per colour-word class (orders n below 32, 64,
+ *     96, 128) whose walk groups take the runs' walks in turn, so one run's tail
+ *     is filled with the next run's walks; the rest of each generation runs on
+ *     the run's own stream.  A class whose first handle has automatic launch
+ *     knobs gets them from plse_autotune on its largest instance (the handles
+ *     keep them).  Every generation waits for the slowest run.
+ * max_inflight = 0 means concurrent with 16 runs.  Runs of a batch (and of the
+ * request server) share the device, so their Alg. 4 uses one kernel pair per
+ * chunk of 128 candidates instead of the single cooperative launch of a run
+ * alone, which would wait for every other run's kernels to leave the device.
+ * best_grids (may be NULL, entries may be NULL): host int8
+ * [n_i*n_i] outputs as plse_solve.  results: host [count].  Every job's result
+ * equals that of plse_solve with the same arguments.  Blocks until every job is
+ * done; returns the first job error (in index order) or PLSE_OK;
+ * results[i].status holds each job's own code. */
+#define PLSE_BATCH_LOCKSTEP (-1)
 int  plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count, int max_inflight,
                       int8_t *const *best_grids, plse_result *results);
 

@@ -121,8 +121,9 @@ int upload_instance(plse_instance *h)
     const size_t o_rv = off; off = up256(off + 2 * (size_t)nv + 2);
     const size_t o_cp = off; off = up256(off + 4 * (size_t)(n + 1));
     const size_t o_cv = off; off = up256(off + 2 * (size_t)nv + 2);
-    const size_t o_ar = off; off = up256(off + 16 * (size_t)n);
+    const size_t o_ar = off; off = off + 16 * (size_t)n;          // columns right after rows
     const size_t o_ac = off; off = up256(off + 16 * (size_t)n);
+    const size_t o_ll = off; off = up256(off + 2 * (size_t)n);
     cudaError_t e = dev_malloc(&h->inst_mem, off, cudaStreamLegacy);
     if (e != cudaSuccess) return fail(h, PLSE_ENOMEM, "instance upload: %s", cudaGetErrorString(e));
     h->inst_bytes = off;
@@ -138,6 +139,8 @@ int upload_instance(plse_instance *h)
     memcpy(img.data() + o_ac, h->allow_col.data(), 16 * (size_t)n);
     memcpy(img.data() + o_rp, h->row_ptr.data(), 4 * (size_t)(n + 1));
     memcpy(img.data() + o_cp, h->col_ptr.data(), 4 * (size_t)(n + 1));
+    for (int l = 0; l < 2 * n; ++l)      // reduced vertices per row, then per column
+        img[o_ll + l] = (uint8_t)(l < n ? h->row_ptr[l + 1] - h->row_ptr[l] : h->col_ptr[l - n + 1] - h->col_ptr[l - n]);
     // A pageable host-to-device copy may return before its DMA has landed, and
     // the legacy stream orders it (and the allocation) for blocking streams only:
     // wait for both, so that kernels on any stream see the whole image.
@@ -162,6 +165,7 @@ int upload_instance(plse_instance *h)
     I.col_v = reinterpret_cast<const uint16_t *>(b + o_cv);
     I.allow_row = reinterpret_cast<const uint4 *>(b + o_ar);
     I.allow_col = reinterpret_cast<const uint4 *>(b + o_ac);
+    I.linelen = b + o_ll;
     return PLSE_OK;
 }
 
@@ -281,6 +285,16 @@ int ensure_ls_workspace(plse_instance *h, int slots, cudaStream_t st)
     return grow(h, ws.counters, ws.counters_cap, 8, true, st);
 }
 
+void set_ls_strides(const DevInst &I, LSArgs &a)
+{
+    a.g_stride = (size_t)I.nv * I.n1p;
+    a.tc_stride = (size_t)I.nv;
+    a.list_stride = (size_t)I.nv;
+    a.xr_stride = 2 * (size_t)I.n * I.n1p;
+    a.hp_stride = hp_words(I);
+    a.sw_stride = sw_bytes(I);
+}
+
 LSArgs ls_args(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0, int gen, int64_t iters,
                uint64_t seed, int flags, int32_t *f_out, int64_t *F_out, plse_walk_stats *stats, const int *skip)
 {
@@ -317,6 +331,7 @@ LSArgs ls_args(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count,
     a.HP = ws.HP;
     a.SW = ws.SW;
     a.slot_clock = ws.slot_clock;
+    set_ls_strides(h->di, a);
     a.work_counter = ws.counters;
     a.error_flag = ws.counters ? ws.counters + 1 : nullptr;
     return a;

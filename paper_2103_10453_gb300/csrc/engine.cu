@@ -142,10 +142,22 @@ int batch_lockstep(plse_instance **hs, const plse_job *jobs, int count, int8_t *
     std::vector<cudaStream_t> st(count, nullptr), cst(kClasses, nullptr);
     std::vector<cudaEvent_t> cev(kClasses, nullptr);
     LSJob *htab = nullptr, *dtab = nullptr;
+    // one scratch set per class, shared by its runs: a walk slot works on one
+    // run at a time, so its tables are sized for the class's largest instance
+    // (the slot clocks keep the evicted-tabu table valid across runs)
+    struct Shared {
+        void *buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        size_t stride[6] = {0, 0, 0, 0, 0, 0};   // G, TC, LIST, XR, HP, SW elements per slot
+    } sh[kClasses];
     int rc = PLSE_OK;
     auto cleanup = [&]() {
         for (auto &q : st) if (q) { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
-        for (auto &q : cst) if (q) { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
+        for (int c = 0; c < kClasses; ++c) {
+            if (cst[c]) cudaStreamSynchronize(cst[c]);
+            for (void *p : sh[c].buf)
+                if (p) cudaFreeAsync(p, cst[c]);
+            if (cst[c]) { cudaStreamSynchronize(cst[c]); cudaStreamDestroy(cst[c]); }
+        }
         for (auto &e : cev) if (e) cudaEventDestroy(e);
         if (dtab) cudaFree(dtab);
         if (htab) cudaFreeHost(htab);
@@ -159,6 +171,30 @@ int batch_lockstep(plse_instance **hs, const plse_job *jobs, int count, int8_t *
     if (!rc && (cudaMallocHost(reinterpret_cast<void **>(&htab), sizeof(LSJob) * count) != cudaSuccess ||
                 cudaMalloc(reinterpret_cast<void **>(&dtab), sizeof(LSJob) * count) != cudaSuccess))
         rc = PLSE_ENOMEM;
+    for (int c = 0; c < kClasses && !rc; ++c) {
+        if (members[c].empty()) continue;
+        size_t *sd = sh[c].stride;
+        for (int i : members[c]) {
+            const DevInst &I = hs[i]->di;
+            LSArgs x{};
+            set_ls_strides(I, x);
+            sd[0] = std::max(sd[0], x.g_stride);
+            sd[1] = std::max(sd[1], x.tc_stride);
+            sd[2] = std::max(sd[2], x.list_stride);
+            sd[3] = std::max(sd[3], x.xr_stride);
+            sd[4] = std::max(sd[4], x.hp_stride);
+            sd[5] = std::max(sd[5], x.sw_stride);
+        }
+        const size_t slots = (size_t)plan[c].slots();
+        const size_t bytes[7] = {4 * slots * sd[0], 8 * slots * sd[1], 2 * slots * sd[2], 2 * slots * sd[3],
+                                 4 * slots * sd[4], slots * sd[5], 4 * slots};
+        for (int k = 0; k < 7 && !rc; ++k)
+            if (dev_malloc(&sh[c].buf[k], bytes[k], cst[c]) != cudaSuccess) rc = PLSE_ENOMEM;
+        // evicted-tabu tables and slot clocks start at zero; the rest is rebuilt by every walk
+        if (!rc && (cudaMemsetAsync(sh[c].buf[0], 0, bytes[0], cst[c]) != cudaSuccess ||
+                    cudaMemsetAsync(sh[c].buf[6], 0, bytes[6], cst[c]) != cudaSuccess))
+            rc = PLSE_ECUDA;
+    }
     if (rc) {
         cleanup();
         return rc;
@@ -197,13 +233,26 @@ int batch_lockstep(plse_instance **hs, const plse_job *jobs, int count, int8_t *
             for (int i : idx) {
                 LSArgs a;
                 cudaEvent_t ready = nullptr;
-                const int e = generation_head(hs[i], plan[c].slots(), a, &ready);
+                const int e = generation_head(hs[i], a, &ready);
                 if (e) {
                     results[i].status = e;
                     note_detail(results[i], hs[i]);
                     live[i] = 0;
                     continue;
                 }
+                a.G = static_cast<uint32_t *>(sh[c].buf[0]);
+                a.TC = static_cast<uint2 *>(sh[c].buf[1]);
+                a.LIST = static_cast<uint16_t *>(sh[c].buf[2]);
+                a.XR = static_cast<uint16_t *>(sh[c].buf[3]);
+                a.HP = static_cast<uint32_t *>(sh[c].buf[4]);
+                a.SW = static_cast<uint8_t *>(sh[c].buf[5]);
+                a.slot_clock = static_cast<uint32_t *>(sh[c].buf[6]);
+                a.g_stride = sh[c].stride[0];
+                a.tc_stride = sh[c].stride[1];
+                a.list_stride = sh[c].stride[2];
+                a.xr_stride = sh[c].stride[3];
+                a.hp_stride = sh[c].stride[4];
+                a.sw_stride = sh[c].stride[5];
                 htab[base[c] + (int)ok.size()] = LSJob{hs[i]->di, a};
                 cudaStreamWaitEvent(cst[c], ready, 0);
                 ok.push_back(i);
@@ -262,7 +311,8 @@ using namespace plse;
 extern "C" int plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count, int max_inflight,
                                 int8_t *const *best_grids, plse_result *results)
 {
-    if (count < 0 || max_inflight < 0 || (count > 0 && (!hs || !jobs || !results))) return PLSE_EINVAL;
+    if (count < 0 || max_inflight < PLSE_BATCH_LOCKSTEP || (count > 0 && (!hs || !jobs || !results)))
+        return PLSE_EINVAL;
     if (count == 0) return PLSE_OK;
     for (int i = 0; i < count; ++i)
         if (!hs[i]) return PLSE_EINVAL;
@@ -271,9 +321,27 @@ extern "C" int plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count
         memset(&results[i], 0, sizeof(plse_result));
         results[i].status = PLSE_EINVAL;
     }
-    // every job on a handle of its own and no cap on runs in flight: one
-    // multi-instance local-search launch per generation and colour-word class
-    bool distinct = max_inflight == 0;
+    // lockstep: every job on a handle of its own, one multi-instance local-search
+    // launch per generation and colour-word class.  Asked for explicitly, or
+    // chosen automatically (max_inflight = 0) for a set of runs of one shape
+    // (same order, |V|, population, generations and iterations: a multi-start),
+    // where no run waits for a slower one at the generation boundary.
+    // the runs share the device: no cooperative launches (they would wait for
+    // every other run's kernels to leave the device)
+    std::vector<char> was_shared(count);
+    for (int i = 0; i < count; ++i) {
+        was_shared[i] = hs[i]->shared_device;
+        hs[i]->shared_device = true;
+    }
+    struct Restore {
+        plse_handle *hs;
+        std::vector<char> &v;
+        ~Restore()
+        {
+            for (size_t i = v.size(); i-- > 0;) hs[i]->shared_device = v[i] != 0;   // first occurrence last
+        }
+    } restore{hs, was_shared};
+    bool distinct = max_inflight == PLSE_BATCH_LOCKSTEP;
     if (distinct) {
         std::unordered_set<plse_instance *> seen;
         for (int i = 0; i < count; ++i) distinct = distinct && seen.insert(hs[i]).second;
@@ -489,6 +557,7 @@ struct plse_server_s {
                     plse_instance *h = nullptr;
                     int rc = plse_create(head.req.n, head.req.grid.data(), &h);
                     if (!rc) rc = plse_set_params(h, &head.req.params);
+                if (h) h->shared_device = true;      // runs beside the other requests
                     if (!rc) {
                         std::lock_guard<std::mutex> lk(mu);
                         rc = plse_set_launch(h, ls_lanes, ls_walks, ls_colourings);

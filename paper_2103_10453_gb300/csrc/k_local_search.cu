@@ -151,21 +151,23 @@ __device__ __forceinline__ void gsync(const Ctx &c)
     else asm volatile("bar.sync %0, %1;" ::"r"(c.g + 1), "r"(GT) : "memory");
 }
 
+// context of thread threadIdx.x in group g: instance data at rc / allow /
+// linelen (shared or global memory), the walk's slot at sb
 template <int GT>
-__device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I, bool s_smem)
+__device__ __forceinline__ Ctx make_ctx_at(const DevInst &I, bool s_smem, const uint16_t *rc, const uint4 *allow,
+                                           const uint8_t *linelen, uint8_t *sb)
 {
     const SmemPlan p = make_plan(I, Grp<GT>::NW, s_smem);
     Ctx c;
-    c.rc = reinterpret_cast<const uint16_t *>(base);
-    c.allow = reinterpret_cast<const uint4 *>(base + align16(2 * (size_t)I.nv));
-    c.linelen = base + align16(2 * (size_t)I.nv) + 32 * (size_t)I.n;
+    c.rc = rc;
+    c.allow = allow;
+    c.linelen = linelen;
     c.g = threadIdx.x / GT;
     c.gt = threadIdx.x % GT;
     c.lane = threadIdx.x & 31;
     c.gl = c.lane & (Grp<GT>::W - 1);
     c.wg = c.gt >> 5;
     c.gm = Grp<GT>::W == 32 ? FULL : (((1u << Grp<GT>::W) - 1u) << (c.lane & ~(Grp<GT>::W - 1)));
-    uint8_t *sb = base + p.inst + p.slot * c.g;
     c.s.S = s_smem ? sb + p.off_S : nullptr;      // global buffer set once the slot is known
     c.s.P01 = reinterpret_cast<uint2 *>(sb + p.off_P01);
     c.s.PH = reinterpret_cast<uint32_t *>(sb + p.off_PH);
@@ -181,6 +183,17 @@ __device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I, bool s_
     c.n = I.n;
     c.cw = colour_words(I.n);
     return c;
+}
+
+// block layout of the single-instance kernel: instance part, then the slots
+template <int GT>
+__device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I, bool s_smem)
+{
+    const SmemPlan p = make_plan(I, Grp<GT>::NW, s_smem);
+    const int g = threadIdx.x / GT;
+    return make_ctx_at<GT>(I, s_smem, reinterpret_cast<const uint16_t *>(base),
+                           reinterpret_cast<const uint4 *>(base + align16(2 * (size_t)I.nv)),
+                           base + align16(2 * (size_t)I.nv) + 32 * (size_t)I.n, base + p.inst + p.slot * g);
 }
 
 struct LaneStats {
@@ -476,10 +489,10 @@ __device__ __forceinline__ void tabu_rebase(const DevInst &I, const Ctx &c)
 }
 
 // (v, k) tabu until relative clock e (inclusive); evicts to G when needed
-__device__ __forceinline__ void tabu_insert(const DevInst &I, const Ctx &c, uint32_t *G, const Clock &ck,
-                                            int v, int k, uint32_t e)
+// as tabu_insert, with v's cache entry x already loaded (by the same thread)
+__device__ __forceinline__ void tabu_insert_entry(const DevInst &I, const Ctx &c, uint32_t *G, const Clock &ck,
+                                                  int v, int k, uint32_t e, const uint2 x)
 {
-    const uint2 x = c.s.tc[v];
     uint32_t e0 = x.x & 0xFFFFu, e1 = x.x >> 16;
     uint32_t c0 = x.y & 0xFFu, c1 = (x.y >> 8) & 0xFFu, em = x.y >> 16;
     if (c0 == (uint32_t)k) {
@@ -496,6 +509,12 @@ __device__ __forceinline__ void tabu_insert(const DevInst &I, const Ctx &c, uint
         if (second) { c1 = (uint32_t)k; e1 = e; } else { c0 = (uint32_t)k; e0 = e; }
     }
     c.s.tc[v] = make_uint2(e0 | (e1 << 16), c0 | (c1 << 8) | (em << 16));
+}
+
+__device__ __forceinline__ void tabu_insert(const DevInst &I, const Ctx &c, uint32_t *G, const Clock &ck,
+                                            int v, int k, uint32_t e)
+{
+    tabu_insert_entry(I, c, G, ck, v, k, e, c.s.tc[v]);
 }
 
 // Word selection by mask arithmetic (a compare-and-select loop over a register
@@ -694,12 +713,14 @@ __device__ __forceinline__ int eval_special(const TabuView &tv, uint32_t trel, i
 // eval while all counts are <= 3: planes 0-1 of R and K only (sums <= 6)
 template <int NWC>
 __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, const uint32_t *G, const Clock &ck,
-                                               uint32_t trel, int v, int mult, int base_unc, int A, int &pairs)
+                                               uint32_t trel, int v, int mult, int base_unc, int A, int &pairs,
+                                               int &iv)
 {
     // the tabu-cache entry (global memory) is loaded first and used last, so its
     // latency overlaps the shared-memory loads and the bit-sliced arithmetic
     const uint2 te = c.s.tc[v];
     const int i = c.s.S[v];
+    iv = i;
     const uint16_t rc = c.rc[v];
     const int r = rc >> 8, cc = rc & 255;
     const uint2 *Pr = c.s.P01 + (size_t)r * NWC, *Pc = c.s.P01 + (size_t)(I.n + cc) * NWC;
@@ -748,10 +769,11 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
 // eval with exact counts (planes 2..6 read where a count reaches 4)
 template <int NWC>
 __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const uint32_t *G, const Clock &ck,
-                                           uint32_t trel, int v, int mult, int base_unc, int A, int &pairs)
+                                           uint32_t trel, int v, int mult, int base_unc, int A, int &pairs, int &iv)
 {
     const uint2 te = c.s.tc[v];
     const int i = c.s.S[v];
+    iv = i;
     const uint16_t rc = c.rc[v];
     const int r = rc >> 8, cc = rc & 255, rl = r, cl = I.n + cc;
     // s = R[r] + K[c] for every colour, bit-sliced
@@ -832,7 +854,7 @@ __device__ __forceinline__ Clock claim_clock(const DevInst &I, const LSArgs &a, 
     gsync<GT>(c);
     uint32_t base = (uint32_t)c.s.scal[1];
     if (base == 0u) {
-        const size_t words = (size_t)I.nv * I.n1p;
+        const size_t words = a.g_stride;              // the slot's whole table
         for (size_t q = c.gt; q < words; q += GT) G[q] = 0u;
         base = 1u;
     }
@@ -975,11 +997,11 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         int live = 0;
         auto consider = [&](int v) {
             ++live;
-            int pairs;
-            const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs)
-                               : eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs);
+            int pairs, iv;
+            const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs, iv)
+                               : eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs, iv);
             st.pairs += pairs;
-            if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, c.s.S[v]));
+            if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, iv));
         };
         if constexpr (NW == 1) {
             int wpos = 0;
@@ -1012,6 +1034,8 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         if (c.wg == 0) {
             const uint16_t rc = c.rc[v];
             const int r = rc >> 8, cc = rc & 255;
+            // v's tabu-cache entry, needed last (tabu_insert), loaded first
+            const uint2 tcv = c.gl == 0 ? c.s.tc[v] : make_uint2(0u, 0u);
             // member-id XOR of (row r | column cc, colour i | j), read first so that
             // its latency overlaps the count updates: lane 0 row/i, 1 column/i,
             // 2 row/j, 3 column/j
@@ -1078,7 +1102,7 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             if (c.gl == 0) {
                 const int k = f + nconf + dconf;
                 const int T = L + tenure_div(a, a.alpha_num * k);
-                tabu_insert(I, c, G, ck, v, i, trel + (uint32_t)T);
+                tabu_insert_entry(I, c, G, ck, v, i, trel + (uint32_t)T, tcv);
             }
             if (NW == 1) {
                 nconf += dconf;
@@ -1183,9 +1207,9 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         int live = 0;
         auto consider = [&](int v) {
             ++live;
-            int pairs;
-            const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs)
-                               : eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs);
+            int pairs, iv;
+            const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs, iv)
+                               : eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs, iv);
             st.pairs += pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, 0));
         };
@@ -1303,17 +1327,16 @@ __device__ __forceinline__ void load_instance(const DevInst &I, uint8_t *smem)
 // The walk groups of one block take walks of one launch (instance I, arguments
 // a) from its counter until none is left.
 template <int NWC, int GT>
-__device__ __forceinline__ void walk_loop(const DevInst &I, const LSArgs &a, int walks, uint8_t *smem)
+__device__ __forceinline__ void walk_loop(const DevInst &I, const LSArgs &a, int walks, Ctx c)
 {
-    Ctx c = make_ctx<GT>(smem, I, a.s_smem != 0);
     if (c.g >= walks) return;
     const int slot = blockIdx.x * walks + c.g;
-    uint32_t *G = a.G + (size_t)slot * I.nv * I.n1p;
-    c.s.tc = a.TC + (size_t)slot * I.nv;
-    c.s.list = a.LIST + (size_t)slot * I.nv;
-    c.s.xr = a.XR + (size_t)slot * 2 * I.n * I.n1p;
-    c.s.HP = a.HP + (size_t)slot * 2 * I.n * c.cw * kHi;
-    if (!a.s_smem) c.s.S = a.SW + (size_t)slot * align16((size_t)I.nv);
+    uint32_t *G = a.G + (size_t)slot * a.g_stride;
+    c.s.tc = a.TC + (size_t)slot * a.tc_stride;
+    c.s.list = a.LIST + (size_t)slot * a.list_stride;
+    c.s.xr = a.XR + (size_t)slot * a.xr_stride;
+    c.s.HP = a.HP + (size_t)slot * a.hp_stride;
+    if (!a.s_smem) c.s.S = a.SW + (size_t)slot * a.sw_stride;
 
     for (;;) {
         if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);
@@ -1373,36 +1396,52 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
     if (a.skip && *a.skip) return;
     load_instance(I, smem);
     __syncthreads();
-    walk_loop<NWC, GT>(I, a, walks, smem);
+    walk_loop<NWC, GT>(I, a, walks, make_ctx<GT>(smem, I, a.s_smem != 0));
 }
 
 // Several launches' worth of walks (one per job, e.g. the same generation of
-// several runs) in one persistent launch: every block takes the jobs in order,
-// loads a job's instance part when it starts on it and moves to the next job
-// as soon as the job's counter runs out, so blocks that finish early fill the
-// tail of one job with walks of the next.  The job descriptors are copied to
-// shared memory; the slots of the block use the job's own layout.
+// several runs) in one persistent launch.  Every walk group takes the jobs in
+// order on its own: it copies a job's descriptor into its part of shared
+// memory, takes the job's walks from the job's counter, and moves to the next
+// job as soon as that counter runs out, so no group waits for another and the
+// tail of one job is filled with walks of the next.  Instance data (vertex
+// coordinates, allowed colours, line lengths) is read from global memory
+// (L1-resident); each group's slot uses its job's own layout within a fixed
+// stride.
+struct JobDesc {
+    DevInst I;
+    LSArgs a;
+};
+
+template <int GT>
+__device__ __forceinline__ void group_sync(int g, unsigned gm)
+{
+    if (Grp<GT>::NW == 1) __syncwarp(gm);
+    else asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(GT) : "memory");
+}
+
 template <int NWC, int GT>
 __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2)
-local_search_multi_kernel(const LSJob *jobs, int njobs, int walks, int s_smem)
+local_search_multi_kernel(const LSJob *jobs, int njobs, int walks, int s_smem, unsigned stride)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ DevInst sI;
-    __shared__ LSArgs sA;
-    __shared__ int sskip;
+    const int g = threadIdx.x / GT, gt = threadIdx.x % GT, lane = threadIdx.x & 31;
+    if (g >= walks) return;
+    const unsigned gm = Grp<GT>::W == 32 ? FULL : (((1u << Grp<GT>::W) - 1u) << (lane & ~(Grp<GT>::W - 1)));
+    uint8_t *gb = smem + (size_t)stride * g;
+    JobDesc *jd = reinterpret_cast<JobDesc *>(gb);
+    uint8_t *sb = gb + align16(sizeof(JobDesc));
     for (int j = 0; j < njobs; ++j) {
-        __syncthreads();                           // the previous job's slots are no longer in use
-        if (threadIdx.x == 0) {
-            sI = jobs[j].I;
-            sA = jobs[j].a;
-            sA.s_smem = s_smem;
-            sskip = sA.skip ? *sA.skip : 0;
+        group_sync<GT>(g, gm);                 // the previous job's descriptor is no longer read
+        if (gt == 0) {
+            jd->I = jobs[j].I;
+            jd->a = jobs[j].a;
+            jd->a.s_smem = s_smem;
         }
-        __syncthreads();
-        if (sskip) continue;
-        load_instance(sI, smem);
-        __syncthreads();
-        walk_loop<NWC, GT>(sI, sA, walks, smem);
+        group_sync<GT>(g, gm);
+        if (jd->a.skip && *jd->a.skip) continue;
+        const DevInst &I = jd->I;
+        walk_loop<NWC, GT>(I, jd->a, walks, make_ctx_at<GT>(I, s_smem != 0, I.rc, I.allow_row, I.linelen, sb));
     }
 }
 
@@ -1488,7 +1527,8 @@ int max_threads_for(int cw)
 template <int NWC, int GT>
 cudaError_t launch_multi_t(const LSJob *jobs, int njobs, const LSLaunch &L, cudaStream_t st)
 {
-    local_search_multi_kernel<NWC, GT><<<L.blocks, GT * L.walks, L.smem, st>>>(jobs, njobs, L.walks, L.s_smem);
+    local_search_multi_kernel<NWC, GT><<<L.blocks, GT * L.walks, L.smem, st>>>(jobs, njobs, L.walks, L.s_smem,
+                                                                                (unsigned)L.stride);
     return cudaGetLastError();
 }
 
@@ -1584,24 +1624,25 @@ LSLaunch plan_local_search_multi(const DevInst *insts, int count, int device, in
     int max_smem = 0, sms = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    // the static part of the kernel's shared memory (job descriptors)
-    const long long budget = (long long)max_smem - (long long)(sizeof(DevInst) + sizeof(LSArgs) + 64);
     long long by_threads = std::max(1, max_threads_for(L.colour_words) / L.group);
     if (max_walks > 0) by_threads = std::min<long long>(by_threads, max_walks);
-    long long walks_s = by_threads, walks_g = by_threads;
+    // one group's part of shared memory: its job descriptor and a slot of the
+    // largest job's layout
+    size_t slot_s = 0, slot_g = 0;
     for (int k = 0; k < count; ++k) {
-        const SmemPlan ps = make_plan(insts[k], warps, true), pg = make_plan(insts[k], warps, false);
-        walks_s = std::min<long long>(walks_s, (budget - (long long)ps.inst) / (long long)ps.slot);
-        walks_g = std::min<long long>(walks_g, (budget - (long long)pg.inst) / (long long)pg.slot);
+        slot_s = std::max(slot_s, make_plan(insts[k], warps, true).slot);
+        slot_g = std::max(slot_g, make_plan(insts[k], warps, false).slot);
     }
+    const size_t desc = align16(sizeof(JobDesc));
+    const long long walks_s = (long long)max_smem / (long long)(desc + slot_s);
+    const long long walks_g = (long long)max_smem / (long long)(desc + slot_g);
     const bool s_smem = s_place == 1 ? true : s_place == 2 ? false : walks_s >= by_threads;
-    const long long walks = s_smem ? walks_s : walks_g;
+    const long long walks = std::min<long long>(s_smem ? walks_s : walks_g, by_threads);
     if (walks < 1) return L;
     L.s_smem = s_smem ? 1 : 0;
     L.walks = (int)walks;
-    size_t smem = 0;
-    for (int k = 0; k < count; ++k) smem = std::max(smem, make_plan(insts[k], warps, s_smem).total(L.walks));
-    L.smem = smem;
+    L.stride = desc + (s_smem ? slot_s : slot_g);
+    L.smem = L.stride * (size_t)L.walks;
     const int threads = L.group * L.walks;
     int per_sm = 0;
     switch (L.colour_words) {

@@ -651,7 +651,7 @@ cudaError_t launch_pop_update(const DevInst &I, int p, const uint32_t *planes, c
     const int nchunks = (m + kChunk - 1) / kChunk;
     NB_DISPATCH(I.nb, (chunk_local_kernel<NBV><<<dim3(nchunks, 4), 256, 0, st>>>(I, planes, ps.order, m, ps.Dloc, skip)));
     bool launched = false;
-    NB_DISPATCH(I.nb, (err = launch_select<NBV>(I, m, p, gamma, ps, skip, st, &launched)));
+    if (ps.cooperative) NB_DISPATCH(I.nb, (err = launch_select<NBV>(I, m, p, gamma, ps, skip, st, &launched)));
     if (err != cudaSuccess) return err;
     if (kernels) *kernels = launched ? 5 : 4 + nchunks + (nchunks - 1);
     if (!launched) {                       // no cooperative launch: one kernel pair per chunk

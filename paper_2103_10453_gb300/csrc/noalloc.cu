@@ -163,6 +163,7 @@ extern "C" int plse_local_search_noalloc(plse_handle h, const uint8_t *S_in, uin
     a.HP = hps;
     a.SW = sws;
     a.slot_clock = clocks;
+    set_ls_strides(h->di, a);
     a.work_counter = counters;
     a.error_flag = counters + 1;
     a.skip = nullptr;

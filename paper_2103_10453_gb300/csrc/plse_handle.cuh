@@ -74,6 +74,8 @@ struct plse_instance {
     plse::PopScratch step_ps;          // Alg. 4 scratch for plse_pop_update
     char *arena = nullptr;             // caller-bound device range (plse_bind_workspace), or null
     size_t arena_size = 0, arena_used = 0;
+    bool shared_device = false;        // runs beside other work (batch, server): no cooperative
+                                       // launches, which would wait for the whole device
     int *noalloc_flag = nullptr;       // check flag of the last plse_local_search_noalloc call (in
                                        // the library's fixed scratch array), read by plse_sync
     cudaEvent_t done_ev = nullptr;     // recorded after the handle's latest enqueued work
@@ -86,6 +88,8 @@ int fail(plse_instance *h, int code, const char *fmt, ...);
 int cuda_fail(plse_instance *h, cudaError_t e, const char *where);
 int max_tenure(const plse_instance *h);
 uint32_t tenure_reciprocal(int alpha_num, int alpha_den, int nv);
+// per-slot strides of a launch's scratch for one instance alone
+void set_ls_strides(const DevInst &I, LSArgs &a);
 // arguments of a local-search launch on the handle's current workspace
 LSArgs ls_args(plse_instance *h, const uint8_t *S_in, uint8_t *S_out, int count, int ind0, int gen, int64_t iters,
                uint64_t seed, int flags, int32_t *f_out, int64_t *F_out, plse_walk_stats *stats, const int *skip);
@@ -134,13 +138,13 @@ int run_poll(plse_instance *h, bool wait);
 int run_drain(plse_instance *h);
 int run_step(plse_instance *h, int generations, cudaStream_t st, int *done_out);
 // one generation of a run split around a local search launched by the caller
-// (several runs' generations in one multi-instance launch): head ensures `slots`
-// walk slots, fills the launch's arguments and records the generation's start
-// event (*ready) on the run's stream; tail, after the caller's launch (event
-// ls_done), enqueues the rest of the generation on the run's stream.  A run with
-// nothing left to issue (finished, generations used) is refused by head with
-// PLSE_ENOTSUP.
-int generation_head(plse_instance *h, int slots, LSArgs &a, cudaEvent_t *ready);
+// (several runs' generations in one multi-instance launch): head fills the
+// launch's arguments (the caller supplies the walk-slot scratch) and records the
+// generation's start event (*ready) on the run's stream; tail, after the caller's
+// launch (event ls_done), enqueues the rest of the generation on the run's
+// stream.  A run with nothing left to issue (finished, generations used) is
+// refused by head with PLSE_ENOTSUP.
+int generation_head(plse_instance *h, LSArgs &a, cudaEvent_t *ready);
 int generation_tail(plse_instance *h, cudaEvent_t ls_done);
 int run_result(plse_instance *h, cudaStream_t st, int8_t *best_grid, int *best_score, plse_solve_stats *stats,
                int32_t *trace_out);

@@ -35,7 +35,8 @@ struct DevInst {
     const int32_t *col_ptr;  // [n + 1]
     const uint16_t *col_v;   // [nv]
     const uint4 *allow_row;  // [n] colours 1..n not prefilled in row r (bit k = colour k)
-    const uint4 *allow_col;  // [n] colours 1..n not prefilled in column c
+    const uint4 *allow_col;  // [n] colours 1..n not prefilled in column c (= allow_row + n)
+    const uint8_t *linelen;  // [2n] reduced vertices per row, then per column
     // D(v) \ {0} = allow_row[row(v)] & allow_col[col(v)] for every reduced vertex
 };
 
@@ -62,6 +63,9 @@ struct LSArgs {
     uint8_t *SW;                  // [slots][nv rounded up to 16] current colourings (when not
                                   // kept in shared memory)
     uint32_t *slot_clock;         // [slots] next free clock value of each slot
+    // elements per walk slot of G, TC, LIST, XR, HP and SW (a launch over several
+    // instances shares one scratch set sized for the largest of them)
+    size_t g_stride, tc_stride, list_stride, xr_stride, hp_stride, sw_stride;
     int *work_counter;            // dynamic walk scheduler, zeroed before launch
     int *error_flag;              // nonzero after a failed device bound check
     const int *skip;              // if non-null and nonzero at launch: return at once
@@ -75,6 +79,7 @@ struct LSLaunch {
     size_t smem = 0;     // dynamic shared memory per block
     int colour_words = 1;// 32-bit words of a colour mask actually used (1..4)
     int s_smem = 1;      // current colourings in the shared-memory slots (else global)
+    size_t stride = 0;   // multi-instance launch: shared memory per walk group
     int slots() const { return blocks * walks; }
 };
 

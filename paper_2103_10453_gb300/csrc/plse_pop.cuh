@@ -35,6 +35,8 @@ struct PopScratch {
     GridBar *bar = nullptr;
     const uint32_t *planes_ref = nullptr;  // set by launch_pop_update for its kernels
     int *error_flag = nullptr;             // set by the caller: a failed pass is reported here
+    bool cooperative = true;               // set by the caller: Alg. 4 in one cooperative launch
+                                           // (false: one kernel pair per chunk)
 };
 
 cudaError_t launch_planes(const DevInst &I, const uint8_t *P, int count, uint32_t *planes, cudaStream_t st);

@@ -432,6 +432,7 @@ static int issue_generation_rest(plse_instance *h, const GenPlan &q)
     CK(cudaEventRecord(s->gev[q.slot][2], st));
     CK(launch_planes(I, q.Pp, p, s->planes[cur] + (size_t)p * stride, st));
     s->ps.error_flag = h->ws.counters ? h->ws.counters + 1 : nullptr;
+    s->ps.cooperative = !h->shared_device;
     long long sel_kernels = 0;
     CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st,
                          &sel_kernels));
@@ -466,7 +467,7 @@ static int issue_generation(plse_instance *h)
     return issue_generation_rest(h, q);
 }
 
-int generation_head(plse_instance *h, int slots, LSArgs &a, cudaEvent_t *ready)
+int generation_head(plse_instance *h, LSArgs &a, cudaEvent_t *ready)
 {
     Session &se = h->session;
     if (!se.active || se.finished || se.issued >= se.max_gens || !h->solver)
@@ -475,7 +476,7 @@ int generation_head(plse_instance *h, int slots, LSArgs &a, cudaEvent_t *ready)
     const cudaStream_t st = se.stream;
     const GenPlan q = plan_generation(h);
     StreamScope scope(h, st);
-    int rc = ensure_ls_workspace(h, slots, st);
+    int rc = ensure_counters(h, st);
     if (rc) return rc;
     a = ls_args(h, s->SO, q.Pp, q.p, 0, q.g, se.iters, se.seed, q.flags, s->fprime, nullptr, s->wstats, q.skip);
     CK(cudaMemsetAsync(a.work_counter, 0, sizeof(int), st));

@@ -367,9 +367,16 @@ def smem_bandwidth(iters=4096):
     return bw.value, ms.value
 
 
-def solve_batch(instances, jobs, max_inflight=0):
-    """plse_solve_batch: job i = (pop, generations, iters, seed) on instances[i].
-    Returns (list of result dicts with 'best_grid', first error code)."""
+PLSE_BATCH_LOCKSTEP = -1
+
+
+def solve_batch(instances, jobs, max_inflight=0, lockstep=False):
+    """plse_solve_batch: job i = (pop, generations, iters, seed) on instances[i];
+    lockstep=True asks for one multi-instance local-search launch per generation
+    (max_inflight = PLSE_BATCH_LOCKSTEP).  Returns (list of result dicts with
+    'best_grid', first error code)."""
+    if lockstep:
+        max_inflight = PLSE_BATCH_LOCKSTEP
     count = len(instances)
     lib = load()
     hs = (_vp * count)(*[inst.h for inst in instances])

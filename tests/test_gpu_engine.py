@@ -215,15 +215,15 @@ def test_server_admits_by_device_memory(plse):
 
 
 def test_batch_one_launch_per_generation_and_class(plse, oracle_mod):
-    """Distinct handles and no cap on runs in flight: the generations of all runs
-    share one persistent multi-instance local-search launch per colour-word class
+    """Lockstep mode: the generations of all runs share one persistent
+    multi-instance local-search launch per colour-word class
     (here n = 10..25, 40, 70: three classes, uneven populations and stops).
     Every result equals plse_solve alone, and one equals the oracle's Alg. 2."""
     gs = grids() + [inputs.random_insertion(40, 0.6, 21), inputs.cyclic_delete(45, 0.7, 22)[0],
                     inputs.random_insertion(70, 0.7, 23)]
     jobs = JOBS + [(80, 3, 400, 8), (50, 4, 300, 9), (70, 2, 500, 10)]
     insts = [plse.Instance(g) for g in gs]
-    out, rc = plse.solve_batch(insts, jobs)
+    out, rc = plse.solve_batch(insts, jobs, lockstep=True)
     assert rc == plse.PLSE_OK
     for g, job, r in zip(gs, jobs, out):
         assert r["status"] == 0, r["detail"]
@@ -261,3 +261,21 @@ def test_autotune_picks_knobs_without_changing_results(plse, oracle_mod):
     So, _ = I.repair(So)
     assert np.array_equal(after[0][0], So)
     G.close()
+
+
+def test_batch_multistart_both_modes(plse, oracle_mod):
+    """A multi-start (one instance, several seeds) in concurrent and in lockstep
+    mode; each run equals plse_solve alone."""
+    g = inputs.random_insertion(40, 0.6, 77)
+    jobs = [(96, 4, 300, 1 + k) for k in range(6)]
+    insts = [plse.Instance(g) for _ in jobs]
+    out, rc = plse.solve_batch(insts, jobs)
+    assert rc == plse.PLSE_OK
+    for job, r in zip(jobs, out):
+        same(r, alone(plse, g, job))
+    out, rc = plse.solve_batch(insts, jobs, lockstep=True)
+    assert rc == plse.PLSE_OK
+    for job, r in zip(jobs, out):
+        same(r, alone(plse, g, job))
+    for G in insts:
+        G.close()
