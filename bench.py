@@ -179,9 +179,9 @@ def measured_peaks():
 # DRAM bytes per tabu move of local_search_kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a launch with walks as long
 # as the benchmark's (bench.py --ls-case 0.3 --pop 2432 --ls-iters 34300
-# --steps 1: 467.8 MB for 2.972e7 moves); scaled to a benchmark launch by its
-# moves.  None whenever the kernel has changed since the capture.
-LS_DRAM_BYTES_PER_MOVE = (216190464 + 251600896) / 29.7232e6   # 15.74 B per move
+# --steps 1: 107.0 MB + 249.1 MB for 2.972e7 moves); scaled to a benchmark
+# launch by its moves.  None whenever the kernel has changed since the capture.
+LS_DRAM_BYTES_PER_MOVE = (107042816 + 249078272) / 29.7234e6   # 11.98 B per move
 
 
 def walk_bytes(w):
