@@ -1326,7 +1326,9 @@ __device__ __forceinline__ void load_instance(const DevInst &I, uint8_t *smem)
 
 // The walk groups of one block take walks of one launch (instance I, arguments
 // a) from its counter until none is left.
-template <int NWC, int GT>
+// PAIRED (single-instance launches with GT = 16): the two walks of a warp are
+// pulled together and start together, so that their iterations run side by side
+template <int NWC, int GT, bool PAIRED>
 __device__ __forceinline__ void walk_loop(const DevInst &I, const LSArgs &a, int walks, Ctx c)
 {
     if (c.g >= walks) return;
@@ -1339,11 +1341,24 @@ __device__ __forceinline__ void walk_loop(const DevInst &I, const LSArgs &a, int
     if (!a.s_smem) c.s.S = a.SW + (size_t)slot * a.sw_stride;
 
     for (;;) {
-        if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);
-        gsync<GT>(c);
-        const int wk = c.s.scal[7];
-        gsync<GT>(c);
-        if (wk >= a.count) break;
+        int wk;
+        if constexpr (PAIRED) {
+            // one pull of two walks per warp; a half without a walk waits for its
+            // partner's (the launch holds an even number of 16-lane groups)
+            __syncwarp(FULL);
+            int base = 0;
+            if (c.lane == 0) base = atomicAdd(a.work_counter, 2);
+            base = __shfl_sync(FULL, base, 0);
+            if (base >= a.count) break;
+            wk = base + (c.lane >> 4);
+            if (wk >= a.count) continue;
+        } else {
+            if (c.gt == 0) c.s.scal[7] = atomicAdd(a.work_counter, 1);
+            gsync<GT>(c);
+            wk = c.s.scal[7];
+            gsync<GT>(c);
+            if (wk >= a.count) break;
+        }
         const int ind = a.ind0 + wk;
         const uint8_t *gin = a.S_in + (size_t)wk * I.nv;
         uint8_t *gout = a.S_out + (size_t)wk * I.nv;
@@ -1396,7 +1411,7 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
     if (a.skip && *a.skip) return;
     load_instance(I, smem);
     __syncthreads();
-    walk_loop<NWC, GT>(I, a, walks, make_ctx<GT>(smem, I, a.s_smem != 0));
+    walk_loop<NWC, GT, GT == 16>(I, a, walks, make_ctx<GT>(smem, I, a.s_smem != 0));
 }
 
 // Several launches' worth of walks (one per job, e.g. the same generation of
@@ -1441,7 +1456,7 @@ local_search_multi_kernel(const LSJob *jobs, int njobs, int walks, int s_smem, u
         group_sync<GT>(g, gm);
         if (jd->a.skip && *jd->a.skip) continue;
         const DevInst &I = jd->I;
-        walk_loop<NWC, GT>(I, jd->a, walks, make_ctx_at<GT>(I, s_smem != 0, I.rc, I.allow_row, I.linelen, sb));
+        walk_loop<NWC, GT, false>(I, jd->a, walks, make_ctx_at<GT>(I, s_smem != 0, I.rc, I.allow_row, I.linelen, sb));
     }
 }
 
@@ -1592,6 +1607,7 @@ LSLaunch plan_local_search(const DevInst &I, int device, int count, int group, i
     const long long walks_g = ((long long)max_smem - (long long)pg.inst) / (long long)pg.slot;
     bool s_smem = s_place == 1 ? true : s_place == 2 ? false : walks_s >= by_threads;
     long long walks = std::min<long long>(s_smem ? walks_s : walks_g, by_threads);
+    if (L.group == 16) walks &= ~1ll;              // 16-lane groups run in pairs, one pair per warp
     if (walks < 1) return L;
     const SmemPlan &p = s_smem ? ps : pg;
     L.s_smem = s_smem ? 1 : 0;
