@@ -75,6 +75,36 @@ def test_issue_query_loop_equals_blocking_run(plse):
         G.close()
 
 
+def test_concurrent_runs_on_streams_equal_runs_alone(plse):
+    """Several runs driven by plse_run_issue on their own streams at once, with
+    and without plse_set_shared_device (per-chunk Alg. 4 kernels instead of the
+    cooperative launch), give each run's result alone; the population is large
+    enough for several Alg. 4 chunks."""
+    import torch
+    gs = grids()[:3]
+    jobs = [(300, 4, 150, 7), (260, 3, 120, 8), (200, 4, 100, 9)]
+    refs = [alone(plse, g, j) for g, j in zip(gs, jobs)]
+    for shared in (False, True):
+        insts, streams = [], []
+        for g, (pop, gens, iters, seed) in zip(gs, jobs):
+            G = plse.Instance(g)
+            G.set_shared_device(shared)
+            s = torch.cuda.Stream()
+            G.run_begin(pop, gens, iters, seed, stream=s)
+            insts.append(G)
+            streams.append(s)
+        while True:
+            done = True
+            for G, s in zip(insts, streams):
+                G.run_issue(stream=s)
+                done = G.run_query()[0] and done
+            if done:
+                break
+        for G, s, ref in zip(insts, streams, refs):
+            same(G.run_result(stream=s), ref)
+            G.close()
+
+
 def test_batch_matches_solve_alone_and_oracle(plse, oracle_mod):
     gs = grids()
     insts = [plse.Instance(g) for g in gs]
