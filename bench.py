@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--pop", type=int, default=POP)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serial", action="store_true",
+                    help="run the five instances' generations one after another on one stream "
+                         "(cooperative Alg. 4) instead of on five streams at once")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ls-case", type=float, default=None, metavar="R",
                     help="small profiling case instead of the benchmark: steady-state phase-1 local "
@@ -184,6 +187,42 @@ def measured_peaks():
 LS_DRAM_BYTES_PER_MOVE = (107042816 + 249078272) / 29.7234e6   # 11.98 B per move
 
 
+def union_ms(intervals):
+    """Length of the union of [start, end] intervals (ms): the time during which
+    at least one of them was running."""
+    total, cur_s, cur_e = 0.0, None, None
+    for a, b in sorted((float(a), float(b)) for a, b in intervals):
+        if b <= a:
+            continue
+        if cur_e is None or a > cur_e:
+            if cur_e is not None:
+                total += cur_e - cur_s
+            cur_s, cur_e = a, b
+        else:
+            cur_e = max(cur_e, b)
+    if cur_e is not None:
+        total += cur_e - cur_s
+    return total
+
+
+def drive_runs(insts, streams, generations):
+    """Issues `generations` more generations of every run, each on its own
+    stream, refilling whichever run has room (two generations in flight per
+    run), and returns once all are enqueued."""
+    left = [generations] * len(insts)
+    while any(left):
+        progressed = False
+        for k, (G, st) in enumerate(zip(insts, streams)):
+            if left[k] == 0:
+                continue
+            G.run_query()
+            if G.run_issue(stream=st):
+                left[k] -= 1
+                progressed = True
+        if not progressed:
+            time.sleep(0.0002)
+
+
 def walk_bytes(w):
     """Algorithmic bytes of tabu moves (explicit-gamma accounting): per scanned
     candidate 1 B colour, per scanned (v, j) pair 1 B gamma + 2 B tabu expiry,
@@ -206,23 +245,34 @@ def run_gpu(args):
     seed = 1 + rank
 
     grids = [inputs.n70(r) for r in RATIOS]
-    insts = []
+    ref_ev = torch.cuda.Event(enable_timing=True)       # time origin of the local-search timeline
+    ref_ev.record(stream)
+    torch.cuda.synchronize()
+    insts, streams = [], []
     for g in grids:
         G = plse.Instance(g)
         prm = plse.default_params(stop_at_bound=0)
         G.set_params(prm)
         if args.launch:
             G.set_launch(*[int(x) for x in args.launch.split(",")])
-        G.run_begin(args.pop, args.warmup + args.steps + 1, 10 * G.nv, seed)
+        st = None if args.serial else torch.cuda.Stream(device=dev)
+        if st is not None:
+            G.set_shared_device(True)
+        G.run_begin(args.pop, args.warmup + args.steps + 1, 10 * G.nv, seed, stream=st)
         insts.append(G)
+        streams.append(st)
 
-    def step():
-        for G in insts:
-            G.run_step(1)
+    def steps(k):
+        # one step = one generation of each of the five runs
+        if args.serial:
+            for _ in range(k):
+                for G in insts:
+                    G.run_step(1)
+        else:
+            drive_runs(insts, streams, k)
 
-    for _ in range(args.warmup):
-        step()
-    before = [G.run_result() for G in insts]
+    steps(args.warmup)
+    before = [G.run_result(stream=st) for G, st in zip(insts, streams)]
 
     if world > 1:
         tdist.barrier()
@@ -232,15 +282,23 @@ def run_gpu(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for st in streams:
+        if st is not None:
+            st.wait_stream(stream)
+    steps(args.steps)
+    for st in streams:
+        if st is not None:
+            stream.wait_stream(st)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     if world > 1:
         tdist.barrier()
-    after = [G.run_result() for G in insts]
+    after = [G.run_result(stream=st) for G, st in zip(insts, streams)]
+    # when the local-search launches of the timed generations ran (ms after ref_ev)
+    timeline = [G.run_timeline(ref_ev, args.warmup, args.steps) for G in insts]
+    ls_busy_ms = union_ms([tuple(iv) for tl in timeline for iv in tl])
 
     moves = sum(a["walks"]["moves"] - b["walks"]["moves"] for a, b in zip(after, before))
     wdelta = {k: sum(a["walks"][k] - b["walks"][k] for a, b in zip(after, before))
@@ -276,7 +334,10 @@ def run_gpu(args):
     smem_derived = sm_count * 128 * sm_max * 1e6 / 1e9
     bytes_alg = walk_bytes(wdelta)
     launches_ls = len(insts) * args.steps
-    achieved = bytes_alg / (ls_ms / 1e3) / 1e9 if ls_ms > 0 else None
+    # the local-search launches of different runs overlap on five streams: the
+    # kernel's time is the union of their intervals (equal to the sum of their
+    # durations when they run one after another)
+    achieved = bytes_alg / (ls_busy_ms / 1e3) / 1e9 if ls_busy_ms > 0 else None
     roofline = {"bound": "smem", "achieved": round(achieved, 1) if achieved else None,
                 "peak": round(smem_peak, 1), "unit": "GB/s",
                 "frac": round(achieved / smem_peak, 4) if achieved else None,
@@ -291,7 +352,13 @@ def run_gpu(args):
                                 "derived bound %d SMs x 128 B/clk x %.0f MHz = %.1f GB/s"
                                 % (probe_clocks.get("sm_mhz"), sm_count, sm_max, smem_derived)),
                 "bytes_per_launch": round(bytes_alg / launches_ls),
-                "ms_per_launch": round(ls_ms / launches_ls, 3),
+                "ms_per_launch": round(ls_busy_ms / launches_ls, 3),
+                "ms_busy": round(ls_busy_ms, 2),
+                "busy_share_of_step": round(ls_busy_ms / ms, 4) if ms > 0 else None,
+                "ms_launch_durations_sum": round(ls_ms, 2),
+                "time_note": ("ms_per_launch = the time during which any local-search launch of the "
+                              "timed steps ran (union of their CUDA-event intervals on their own "
+                              "streams) / launches; achieved = algorithmic bytes / that time"),
                 "moves_per_launch": round(wdelta["moves"] / launches_ls)}
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -299,6 +366,9 @@ def run_gpu(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
            "data": "synthetic (seeded instances of the paper's benchmark shapes; random initial colourings)",
            "config": dict(workload_config(args.pop), parallelism="replicas" if world > 1 else "single"),
+           "schedule": ("the five runs one after another on one stream, cooperative Alg. 4" if args.serial
+                        else "the five runs on five CUDA streams at once (plse_run_issue), Alg. 4 as "
+                             "per-chunk kernels (plse_set_shared_device)"),
            "roofline": roofline, "clocks": clk, "gpu_launches": launches,
            "per_instance": per_inst}
 
@@ -316,29 +386,42 @@ def run_gpu(args):
 
 
 def run_e2e(args, plse, inputs, seed):
-    """Same metric through the public C ABI with host buffers: plse_create
-    (host grid -> device), one-generation plse_solve_ex per instance, best grid
-    back to the host; wall clock around all of it."""
+    """Same metric through the public C ABI with host buffers: plse_create of
+    each instance (host grid -> device), one plse_solve_batch call solving the
+    five one-generation jobs at once (concurrent runs), best grids back to the
+    host; wall clock around all of it.  With --serial: one plse_solve_ex per
+    instance, one after another."""
     import numpy as np
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     moves, h2d, d2h = 0, 0, 0
+    insts = []
     for r in RATIOS:
         g = np.ascontiguousarray(inputs.n70(r), dtype=np.int8)
         G = plse.Instance(g)
         G.set_params(plse.default_params(stop_at_bound=0))
-        res = G.solve(args.pop, 1, 10 * G.nv, seed, with_stats=True)
-        moves += res["walks"]["moves"]
+        insts.append(G)
         h2d += g.nbytes + G.nv * 24 + 2 * 70 * 20          # grid + uploaded instance image
-        d2h += res["best_grid"].nbytes + 8 * res["generations"] + 64
+    if args.serial:
+        res = [G.solve(args.pop, 1, 10 * G.nv, seed, with_stats=True) for G in insts]
+    else:
+        res, rc = plse.solve_batch(insts, [(args.pop, 1, 10 * G.nv, seed) for G in insts],
+                                   max_inflight=len(insts))
+        if rc != plse.PLSE_OK:
+            raise plse.PlseError(rc, "plse_solve_batch")
+    for r in res:
+        moves += r["walks"]["moves"]
+        d2h += r["best_grid"].nbytes + 8 * r["generations"] + 64
+    for G in insts:
         G.close()
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     return {"value": round(moves / secs, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h,
-            "note": "one generation (from random colourings) of each of the five instances, "
-                    "host grid in, host best grid out, wall clock"}
+            "note": ("one generation (from random colourings) of each of the five instances through "
+                     "%s, host grid in, host best grid out, wall clock"
+                     % ("plse_solve_ex one by one" if args.serial else "one plse_solve_batch call"))}
 
 
 # ---------------------------------------------------------------------------

@@ -232,6 +232,17 @@ int  plse_run_population(plse_handle h, int which, uint8_t *dst, void *stream);
 int  plse_run_issue(plse_handle h, void *stream, int *issued);
 int  plse_run_query(plse_handle h, int *done, int *generations, int *in_flight);
 
+/* plse_run_timeline -- when each local-search launch of the run ran: for the
+ * completed generations first .. first+count-1 (counted from plse_run_begin),
+ * ls_start_end[2k], ls_start_end[2k+1] = start and end of generation
+ * first+k's local-search launch, in milliseconds after `ref_event` (a
+ * cudaEvent_t with timing that the caller recorded on the run's device before
+ * calling plse_run_begin, and that has completed).  Lets a caller that
+ * runs several runs at once measure the time during which any local search ran.
+ * Waits for the run's enqueued generations; PLSE_EINVAL if a generation in the
+ * range has not run or the event has not completed. */
+int  plse_run_timeline(plse_handle h, void *ref_event, int first, int count, float *ls_start_end);
+
 /* ---- many jobs at once ------------------------------------------------------
  * A job is one plse_solve: population, generations, phase-1 iterations, seed. */
 typedef struct {

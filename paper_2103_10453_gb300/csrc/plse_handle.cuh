@@ -43,6 +43,7 @@ struct Session {
     cudaStream_t stream = nullptr;
     double ms_ls = 0;
     long long launches = 0;
+    std::vector<float> ls_iv;   // per completed generation: local-search start, end (ms after run begin)
 };
 
 }  // namespace plse

@@ -521,9 +521,13 @@ int run_poll(plse_instance *h, bool wait)
         }
         ++se.polled;
         if (se.finished) continue;   // enqueued past the stop: skipped on the device
-        float ms = 0;
+        float ms = 0, t0 = 0, t1 = 0;
         CK(cudaEventElapsedTime(&ms, s->gev[slot][0], s->gev[slot][1]));
+        CK(cudaEventElapsedTime(&t0, s->ev[0], s->gev[slot][0]));
+        CK(cudaEventElapsedTime(&t1, s->ev[0], s->gev[slot][1]));
         se.ms_ls += ms;
+        se.ls_iv.push_back(t0);
+        se.ls_iv.push_back(t1);
         se.gen += 1;
         if ((h->params.stop_at_bound && s->hflag[2 * slot + 1]) || se.gen >= se.max_gens) se.finished = 1;
     }
@@ -700,6 +704,27 @@ int plse_run_population(plse_handle h, int which, uint8_t *dst, void *stream)
     const uint8_t *src = which == PLSE_RUN_POPULATION ? s->Pall[se.cur] : s->SO;
     if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
+    return PLSE_OK;
+}
+
+int plse_run_timeline(plse_handle h, void *ref_event, int first, int count, float *ls_start_end)
+{
+    if (!h || !ref_event || first < 0 || count < 0 || (count > 0 && !ls_start_end)) return PLSE_EINVAL;
+    Session &se = h->session;
+    if (!se.active || !h->solver) return fail(h, PLSE_EINVAL, "plse_run_timeline: no run in progress");
+    int rc = run_drain(h);
+    if (rc) return rc;
+    if ((long long)first + count > (long long)se.ls_iv.size() / 2)
+        return fail(h, PLSE_EINVAL, "plse_run_timeline: generations not run");
+    if (count == 0) return PLSE_OK;
+    const cudaEvent_t ref = static_cast<cudaEvent_t>(ref_event);
+    const cudaError_t q = cudaEventQuery(ref);
+    if (q != cudaSuccess)
+        return q == cudaErrorNotReady ? fail(h, PLSE_EINVAL, "plse_run_timeline: reference event not complete")
+                                      : cuda_fail(h, q, "plse_run_timeline");
+    float off = 0;
+    CK(cudaEventElapsedTime(&off, ref, h->solver->ev[0]));
+    for (int k = 0; k < 2 * count; ++k) ls_start_end[k] = off + se.ls_iv[2 * (size_t)first + k];
     return PLSE_OK;
 }
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "plse_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
     "plse_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "plse_set_shared_device": (C.c_int, [_vp, C.c_int]),
+    "plse_run_timeline": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.POINTER(C.c_float)]),
     "plse_default_params": (None, [C.POINTER(Params)]),
     "plse_set_params": (C.c_int, [_vp, C.POINTER(Params)]),
     "plse_get_params": (C.c_int, [_vp, C.POINTER(Params)]),
@@ -306,6 +307,15 @@ class Instance:
         done, gens, inflight = C.c_int(), C.c_int(), C.c_int()
         self._check(self.lib.plse_run_query(self.h, C.byref(done), C.byref(gens), C.byref(inflight)))
         return bool(done.value), int(gens.value), int(inflight.value)
+
+    def run_timeline(self, ref_event, first, count):
+        """plse_run_timeline: [count, 2] float array, start and end (ms after the
+        completed torch.cuda.Event ``ref_event``) of the local-search launches of
+        generations first .. first+count-1."""
+        out = np.zeros((max(count, 1), 2), dtype=np.float32)
+        self._check(self.lib.plse_run_timeline(self.h, C.c_void_p(ref_event.cuda_event), first, count,
+                                               out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out[:count]
 
     def run_result(self, stream=None, trace=False):
         grid = np.zeros((self.n, self.n), dtype=np.int8)

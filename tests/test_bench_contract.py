@@ -30,3 +30,21 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_local_search_busy_time_is_the_union_of_the_launch_intervals():
+    """The benchmark's kernel time when launches of several runs overlap: the
+    length of the union of their [start, end] intervals."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.union_ms([]) == 0.0
+    assert bench.union_ms([(0, 1), (2, 3)]) == 2.0                    # disjoint: the sum
+    assert bench.union_ms([(0, 4), (1, 2), (3, 5)]) == 5.0             # nested and chained
+    assert bench.union_ms([(3, 5), (0, 1), (0.5, 3)]) == 5.0           # order does not matter
+    assert bench.union_ms([(1, 1), (2, 1.5)]) == 0.0                   # empty intervals
+    import random
+    rnd = random.Random(5)
+    iv = [(a, a + rnd.uniform(0, 3)) for a in (rnd.uniform(0, 20) for _ in range(40))]
+    grid = [k * 0.001 for k in range(26000)]
+    covered = sum(1 for t in grid if any(a <= t < b for a, b in iv)) * 0.001
+    assert abs(bench.union_ms(iv) - covered) < 0.05

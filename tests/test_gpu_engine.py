@@ -105,6 +105,28 @@ def test_concurrent_runs_on_streams_equal_runs_alone(plse):
             G.close()
 
 
+def test_run_timeline_gives_each_generations_local_search_interval(plse):
+    import torch
+    ref = torch.cuda.Event(enable_timing=True)
+    ref.record()
+    torch.cuda.synchronize()
+    G = plse.Instance(grids()[4])
+    G.set_params(plse.default_params(stop_at_bound=0))
+    G.run_begin(48, 4, 150, 3)
+    G.run_step(3)
+    tl = G.run_timeline(ref, 0, 3)
+    res = G.run_result()
+    assert tl.shape == (3, 2)
+    assert np.all(tl[:, 0] > 0) and np.all(tl[:, 1] > tl[:, 0])
+    assert np.all(tl[1:, 0] >= tl[:-1, 1])                 # one stream: one after another
+    assert abs(float((tl[:, 1] - tl[:, 0]).sum()) - res["ms_local_search"]) < 1e-2
+    assert np.array_equal(G.run_timeline(ref, 1, 2), tl[1:])
+    with pytest.raises(plse.PlseError) as e:
+        G.run_timeline(ref, 2, 2)                           # generation 3 has not run
+    assert e.value.code == plse.PLSE_EINVAL
+    G.close()
+
+
 def test_batch_matches_solve_alone_and_oracle(plse, oracle_mod):
     gs = grids()
     insts = [plse.Instance(g) for g in gs]
