@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serial", action="store_true",
                     help="run the five instances' generations one after another on one stream "
-                         "(cooperative Alg. 4) instead of on five streams at once")
+                         "instead of on five streams at once")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ls-case", type=float, default=None, metavar="R",
                     help="small profiling case instead of the benchmark: steady-state phase-1 local "
@@ -256,8 +256,6 @@ def run_gpu(args):
         if args.launch:
             G.set_launch(*[int(x) for x in args.launch.split(",")])
         st = None if args.serial else torch.cuda.Stream(device=dev)
-        if st is not None:
-            G.set_shared_device(True)
         G.run_begin(args.pop, args.warmup + args.steps + 1, 10 * G.nv, seed, stream=st)
         insts.append(G)
         streams.append(st)
@@ -366,9 +364,8 @@ def run_gpu(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
            "data": "synthetic (seeded instances of the paper's benchmark shapes; random initial colourings)",
            "config": dict(workload_config(args.pop), parallelism="replicas" if world > 1 else "single"),
-           "schedule": ("the five runs one after another on one stream, cooperative Alg. 4" if args.serial
-                        else "the five runs on five CUDA streams at once (plse_run_issue), Alg. 4 as "
-                             "per-chunk kernels (plse_set_shared_device)"),
+           "schedule": ("the five runs one after another on one stream" if args.serial
+                        else "the five runs on five CUDA streams at once (plse_run_issue)"),
            "roofline": roofline, "clocks": clk, "gpu_launches": launches,
            "per_instance": per_inst}
 

@@ -130,17 +130,6 @@ int  plse_get_params(plse_handle h, plse_params *p);
  * automatic (shared memory unless that would cut the walks per block). */
 int  plse_set_launch(plse_handle h, int ls_lanes, int ls_walks, int ls_colourings);
 
-/* plse_set_shared_device -- declares (shared = 1) that this handle's runs share
- * the GPU with other work running at the same time (several runs driven by
- * plse_run_issue on their own streams, other kernels of the caller's): the
- * population update of Alg. 4 then runs as a pair of ordinary kernels per
- * chunk of 128 candidates instead of one cooperative launch, whose grid
- * barrier needs every block of the grid resident at once and would stall
- * behind the other work.  shared = 0 (the default) restores the cooperative
- * launch.  Results are the same either way.  plse_solve_batch and plse_server
- * set it on the handles they run. */
-int  plse_set_shared_device(plse_handle h, int shared);
-
 /* plse_autotune -- picks the launch knobs above for runs of `pop` individuals
  * on this handle's instance by timing short probe launches of the local search
  * (`probe_iters` phase-1 iterations on `pop` colourings, several candidate

@@ -474,13 +474,6 @@ int plse_set_launch(plse_handle h, int ls_lanes, int ls_walks, int ls_colourings
     return PLSE_OK;
 }
 
-int plse_set_shared_device(plse_handle h, int shared)
-{
-    if (!h || (shared != 0 && shared != 1)) return PLSE_EINVAL;
-    h->shared_device = shared != 0;
-    return PLSE_OK;
-}
-
 int plse_workspace_size(plse_handle h, int pop, int max_generations, size_t *bytes)
 {
     if (!h || !bytes || pop < 2 || pop > 65535 || max_generations < 0 || max_generations > 65534)

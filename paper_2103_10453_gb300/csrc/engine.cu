@@ -321,26 +321,9 @@ extern "C" int plse_solve_batch(plse_handle *hs, const plse_job *jobs, int count
         memset(&results[i], 0, sizeof(plse_result));
         results[i].status = PLSE_EINVAL;
     }
-    // lockstep: every job on a handle of its own, one multi-instance local-search
-    // launch per generation and colour-word class.  Asked for explicitly, or
-    // chosen automatically (max_inflight = 0) for a set of runs of one shape
-    // (same order, |V|, population, generations and iterations: a multi-start),
-    // where no run waits for a slower one at the generation boundary.
-    // the runs share the device: no cooperative launches (they would wait for
-    // every other run's kernels to leave the device)
-    std::vector<char> was_shared(count);
-    for (int i = 0; i < count; ++i) {
-        was_shared[i] = hs[i]->shared_device;
-        hs[i]->shared_device = true;
-    }
-    struct Restore {
-        plse_handle *hs;
-        std::vector<char> &v;
-        ~Restore()
-        {
-            for (size_t i = v.size(); i-- > 0;) hs[i]->shared_device = v[i] != 0;   // first occurrence last
-        }
-    } restore{hs, was_shared};
+    // lockstep (max_inflight = PLSE_BATCH_LOCKSTEP, every job on a handle of its
+    // own): one multi-instance local-search launch per generation and colour-word
+    // class; otherwise concurrent runs, each on a stream of its own.
     bool distinct = max_inflight == PLSE_BATCH_LOCKSTEP;
     if (distinct) {
         std::unordered_set<plse_instance *> seen;
@@ -557,7 +540,6 @@ struct plse_server_s {
                     plse_instance *h = nullptr;
                     int rc = plse_create(head.req.n, head.req.grid.data(), &h);
                     if (!rc) rc = plse_set_params(h, &head.req.params);
-                if (h) h->shared_device = true;      // runs beside the other requests
                     if (!rc) {
                         std::lock_guard<std::mutex> lk(mu);
                         rc = plse_set_launch(h, ls_lanes, ls_walks, ls_colourings);

@@ -73,13 +73,20 @@ struct TileSmem {
 // 16-byte row reads stay aligned).
 __device__ __forceinline__ int tile_swz(int slot) { return (slot & 15) << 2; }
 
+struct KeepAll {
+    __device__ __forceinline__ bool operator()(const int (&)[4][4]) const { return true; }
+};
+
 // Distances between rows ra[0..63] and columns cb[0..63] (indices into the
-// plane array; -1 = padding) accumulated into acc[4][4].
-template <int NB>
+// plane array; -1 = padding) accumulated into acc[4][4].  With PRUNE, after
+// every staged chunk of kWC words each thread asks keep(acc) whether one of its
+// pairs still needs the rest of the words; when no thread does, the tile stops
+// there and acc holds partial sums (a lower bound of each distance).
+template <int NB, bool PRUNE = false, class Keep = KeepAll>
 __device__ __forceinline__ void tile_distances(const uint32_t *__restrict__ planesA,
                                                const uint32_t *__restrict__ planesB, int nw,
                                                const int *ra, const int *cb, TileSmem<NB> &sm,
-                                               int (&acc)[4][4])
+                                               int (&acc)[4][4], const Keep &keep = Keep())
 {
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const size_t stride = (size_t)nw * NB;
@@ -87,9 +94,14 @@ __device__ __forceinline__ void tile_distances(const uint32_t *__restrict__ plan
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    bool need = true;
     for (int w0 = 0; w0 < nw; w0 += kWC) {
         const int wc = min(kWC, nw - w0);
-        __syncthreads();
+        if constexpr (PRUNE) {
+            if (!__syncthreads_or(need)) break;      // no pair of the tile can still matter
+        } else {
+            __syncthreads();
+        }
         // stage: 64 rows x wc*NB words for A and for B
         for (int q = tid; q < kTile * kWC * NB; q += 256) {
             const int r = q / (kWC * NB), rest = q % (kWC * NB);
@@ -131,6 +143,7 @@ __device__ __forceinline__ void tile_distances(const uint32_t *__restrict__ plan
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[a][c] += __popc(o[a][c]);
         }
+        if constexpr (PRUNE) need = keep(acc);
     }
 }
 
@@ -217,8 +230,8 @@ __global__ void __launch_bounds__(256) chunk_local_kernel(const DevInst I, const
 // holds positions l, l+32, l+64, l+96 of the chunk with their current minimum
 // distance to the accepted set; the chunk's own distances are staged in shared
 // memory (Dc) so each sequential step costs only shared loads and one shuffle.
-// Values other blocks write during a persistent pass (mind, the state) are read
-// through L2 (ld.global.cg), never from a possibly stale L1 line.
+// Values other blocks write during the pass (mind, the state) are read through
+// L2 (ld.global.cg), never from a possibly stale L1 line.
 __device__ __forceinline__ void resolve_chunk(int chunk, int m, int p, int nv, int gamma, const int32_t *order,
                                               const int32_t *mind, const uint16_t *Dloc, int32_t *acc,
                                               int32_t *rej, SelState *s, uint16_t *Dc)
@@ -237,7 +250,6 @@ __device__ __forceinline__ void resolve_chunk(int chunk, int m, int p, int nv, i
     }
     __syncwarp();
     int nacc = __ldcg(&s->nacc), nrej = __ldcg(&s->nrej);
-    if (lane == 0) s->chunk_acc_start = nacc;
     const int lim = min(kChunk, m - base);
     for (int qpos = 0; qpos < lim && nacc < p; ++qpos) {
         int mine = INT_MAX, cmine = -1;
@@ -267,22 +279,34 @@ __device__ __forceinline__ void resolve_chunk(int chunk, int m, int p, int nv, i
     }
 }
 
-__global__ void __launch_bounds__(32) resolve_chunk_kernel(int chunk, int m, int p, int nv, int gamma,
-                                                           const int32_t *order, const int32_t *mind,
-                                                           const uint16_t *Dloc, int32_t *acc,
-                                                           int32_t *rej, SelState *s, const int *skip)
-{
-    if ((skip && *skip) || s->done) return;
-    __shared__ __align__(16) uint16_t Dc[kChunk * kChunk];
-    resolve_chunk(chunk, m, p, nv, gamma, order, mind, Dloc, acc, rej, s, Dc);
-}
+// Alg. 4 uses a minimum distance only in the test gamma * D > |V|, i.e.
+// D >= cut with cut = floor(|V| / gamma) + 1.  A tile of the minimum-distance
+// update therefore stops counting once every valid pair has reached cut: the
+// minimum it stores is then a partial sum >= cut, which passes the test exactly
+// when the true minimum does, and a minimum below cut is always exact (the tile
+// runs to the end while one of its pairs is below cut).
+struct KeepBelowCut {
+    int cut;
+    bool rv[4], cv[4];
+    __device__ __forceinline__ bool operator()(const int (&acc)[4][4]) const
+    {
+        bool k = false;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) k |= rv[a] && cv[c] && acc[a][c] < cut;
+        return k;
+    }
+};
 
 // min distance of the 64 candidates of tile `tb` after chunk `chunk` to the
-// members accepted in that chunk (acc[a0 .. a1)); every thread of the block
+// members accepted in that chunk (acc[a0 .. a1)), exact below `cut`; every
+// thread of the block
 template <int NB>
 __device__ __forceinline__ void update_mind_tile(const DevInst &I, const uint32_t *planes, int chunk, int tb, int m,
                                                  const int32_t *order, int32_t *mind, const int32_t *accl, int a0,
-                                                 int a1, TileSmem<NB> &sm, int *ra, int *cb, int (*rowmin)[17])
+                                                 int a1, int cut, TileSmem<NB> &sm, int *ra, int *cb,
+                                                 int (*rowmin)[17])
 {
     const int first = (chunk + 1) * kChunk + tb * kTile;
     if (first >= m) return;
@@ -296,8 +320,15 @@ __device__ __forceinline__ void update_mind_tile(const DevInst &I, const uint32_
             cb[threadIdx.x] = ac < a1 ? __ldcg(&accl[ac]) : -1;
         }
         __syncthreads();
+        KeepBelowCut keep;
+        keep.cut = cut;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            keep.rv[q] = ra[4 * ty + q] >= 0;
+            keep.cv[q] = cb[4 * tx + q] >= 0;
+        }
         int acc[4][4];
-        tile_distances<NB>(planes, planes, I.nw, ra, cb, sm, acc);
+        tile_distances<NB, true>(planes, planes, I.nw, ra, cb, sm, acc, keep);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -311,71 +342,58 @@ __device__ __forceinline__ void update_mind_tile(const DevInst &I, const uint32_
         int v = INT_MAX;
         for (int q = 0; q < 16; ++q) v = min(v, rowmin[threadIdx.x][q]);
         const int pos = first + threadIdx.x;
-        if (pos < m) mind[pos] = min(__ldcg(&mind[pos]), v);
+        if (pos < m && v != INT_MAX) atomicMin(&mind[pos], v);   // tiles of several chunks may overlap in time
     }
     __syncthreads();
 }
 
-template <int NB>
-__global__ void __launch_bounds__(256) update_mind_kernel(const DevInst I, const uint32_t *planes,
-                                                          int chunk, int m, const int32_t *order,
-                                                          int32_t *mind, const int32_t *accl,
-                                                          const SelState *s, const int *skip)
+// Alg. 4 after the ranking, as one dataflow launch.  The pass is a fixed list
+// of work items in dependency order: for each chunk k of 128 ranked candidates
+// the item R_k (the sequential greedy of resolve_chunk on chunk k), then one
+// item U_{k,t} per 64-candidate tile t after chunk k (the minimum distances of
+// those candidates to the members accepted in chunk k).  Blocks claim items
+// from one counter in list order.  R_k waits until R_{k-1} and every U_{k',t}
+// covering chunk k (k' < k) have finished; U_{k,t} waits for R_k.  Each wait is
+// on an item claimed earlier, i.e. held by a block that is already running, so
+// the pass completes with any number of resident blocks (no cooperative launch:
+// it can share the GPU with other kernels), and the updates of chunk k overlap
+// the resolution of chunk k+1, which needs only the two tiles covering it.
+// Tiles of different chunks may lower one candidate's minimum at the same time:
+// atomicMin, whose result does not depend on their order.  Every wait is
+// bounded (kFlowSpins polls); a block that gives up sets the error word and
+// leaves, and the blocks waiting behind it leave as soon as they see it.
+constexpr unsigned long long kFlowSpins = 1ull << 24;
+
+// first item of chunk k: chunk k' < C-1 holds 1 + tiles(k') items with
+// tiles(k') = 2 (C-2-k') + e, e = tiles covering the last (partial) chunk
+__device__ __forceinline__ long long flow_start(int k, int C, int e)
 {
-    if ((skip && *skip) || s->done) return;
-    const int a0 = s->chunk_acc_start, a1 = s->nacc;
-    if (a1 <= a0) return;
-    __shared__ TileSmem<NB> sm;
-    __shared__ int ra[kTile], cb[kTile];
-    __shared__ int rowmin[kTile][17];
-    update_mind_tile<NB>(I, planes, chunk, blockIdx.x, m, order, mind, accl, a0, a1, sm, ra, cb, rowmin);
+    return (long long)k * (1 + e) + 2LL * k * (C - 2) - (long long)k * (k - 1);
 }
 
-// Grid-wide barrier of a cooperative launch (every block resident).  Thread 0
-// of each block arrives on a counter; the last one resets it and advances the
-// generation word the others wait on.  The wait is bounded: after kBarrierSpins
-// polls the block records the failure in err and leaves (false), so a broken
-// launch ends with an error instead of spinning forever.
-constexpr unsigned long long kBarrierSpins = 1ull << 24;
-
-__device__ __forceinline__ bool grid_sync(GridBar *b)
+// thread 0: wait until *w >= target; false (error word set) if the bound runs
+// out or another block has already given up
+__device__ __forceinline__ bool flow_wait(const int *w, int target, int *err)
 {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *vg = &b->gen;
-        const unsigned g = *vg;
-        __threadfence();
-        ok = 1;
-        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*vg == g) {
-                if (++spins > kBarrierSpins) {
-                    atomicOr(&b->err, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
+    const volatile int *vw = w;
+    const volatile int *ve = err;
+    unsigned long long spins = 0;
+    while (*vw < target) {
+        if (++spins > kFlowSpins || *ve) {
+            atomicOr(err, 1);
+            return false;
         }
-        __threadfence();
+        __nanosleep(64);
     }
-    __syncthreads();
-    return ok != 0;
+    __threadfence();
+    return true;
 }
 
-// Alg. 4 over all chunks in one cooperative launch: block 0 resolves chunk k,
-// then every block updates the minimum distances of the later candidates to
-// the members just accepted, a grid barrier between the two.
 template <int NB>
-__global__ void __launch_bounds__(256) select_kernel(const DevInst I, const uint32_t *planes, int m, int p,
-                                                     int gamma, const int32_t *order, int32_t *mind,
-                                                     const uint16_t *Dloc, int32_t *acc, int32_t *rej,
-                                                     SelState *s, GridBar *bar, const int *skip)
+__global__ void __launch_bounds__(256) select_flow_kernel(const DevInst I, const uint32_t *planes, int m, int p,
+                                                          int gamma, const int32_t *order, int32_t *mind,
+                                                          const uint16_t *Dloc, int32_t *acc, int32_t *rej,
+                                                          SelState *s, int32_t *flow, const int *skip)
 {
     if (skip && *skip) return;
     extern __shared__ __align__(16) uint8_t dsm[];
@@ -383,30 +401,69 @@ __global__ void __launch_bounds__(256) select_kernel(const DevInst I, const uint
     uint16_t *Dc = reinterpret_cast<uint16_t *>(dsm + sizeof(TileSmem<NB>));
     __shared__ int ra[kTile], cb[kTile];
     __shared__ int rowmin[kTile][17];
-    volatile SelState *vs = s;
-    const int nchunks = (m + kChunk - 1) / kChunk;
-    for (int k = 0; k < nchunks; ++k) {
-        if (blockIdx.x == 0 && threadIdx.x < 32) resolve_chunk(k, m, p, I.nv, gamma, order, mind, Dloc, acc, rej, s, Dc);
-        if (!grid_sync(bar)) return;
-        if (vs->done) break;
-        const int a0 = vs->chunk_acc_start, a1 = vs->nacc;
-        const int rows = m - (k + 1) * kChunk;
-        if (a1 > a0 && rows > 0) {
-            const int tiles = (rows + kTile - 1) / kTile;
-            for (int tb = blockIdx.x; tb < tiles; tb += gridDim.x)
-                update_mind_tile<NB>(I, planes, k, tb, m, order, mind, acc, a0, a1, sm, ra, cb, rowmin);
+    __shared__ int it_k, it_t, it_ok, it_done, it_a0, it_a1;
+    SelFlow *f = reinterpret_cast<SelFlow *>(flow);
+    const int C = (m + kChunk - 1) / kChunk;
+    int *upd = flow + kSelFlowHeader, *accn = flow + kSelFlowHeader + C;
+    const int e = (m - (C - 1) * kChunk + kTile - 1) / kTile;
+    const long long total = flow_start(C - 1, C, e) + 1;
+    const int cut = (int)((long long)I.nv / gamma + 1);     // gamma * D > |V|  <=>  D >= cut
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long x = (long long)atomicAdd(&f->next, 1u);
+            int k = -1, t = 0, ok = 1, done = 0, a0 = 0, a1 = 0;
+            if (x < total) {
+                int lo = 0, hi = C - 1;                  // the last chunk k with flow_start(k) <= x
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (flow_start(mid, C, e) <= x) lo = mid; else hi = mid - 1;
+                }
+                k = lo;
+                t = (int)(x - flow_start(k, C, e)) - 1;  // -1: R_k, else tile t of U_k
+                if (t < 0) {
+                    ok = flow_wait(&f->resolved, k, &f->err) &&
+                         flow_wait(&upd[k], k * (k == C - 1 ? e : 2), &f->err);
+                } else {
+                    ok = flow_wait(&f->resolved, k + 1, &f->err);
+                    if (ok) {
+                        a0 = k ? __ldcg(&accn[k - 1]) : 0;
+                        a1 = __ldcg(&accn[k]);
+                    }
+                }
+                if (ok) done = __ldcg(&s->done);
+            }
+            it_k = k; it_t = t; it_ok = ok; it_done = done; it_a0 = a0; it_a1 = a1;
         }
-        if (!grid_sync(bar)) return;
+        __syncthreads();
+        const int k = it_k, t = it_t;
+        if (k < 0 || !it_ok) return;
+        if (t < 0) {
+            // R_k; thread 0 (lane 0 of the resolving warp) wrote the state, acc and rej
+            if (!it_done && threadIdx.x < 32) resolve_chunk(k, m, p, I.nv, gamma, order, mind, Dloc, acc, rej, s, Dc);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                accn[k] = __ldcg(&s->nacc);
+                __threadfence();
+                atomicAdd(&f->resolved, 1);
+            }
+        } else {
+            if (!it_done && it_a1 > it_a0)
+                update_mind_tile<NB>(I, planes, k, t, m, order, mind, acc, it_a0, it_a1, cut, sm, ra, cb, rowmin);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&upd[k + 1 + t / 2], 1);
+        }
+        __syncthreads();
     }
 }
 
 // fill rule and the final selection list
 __global__ void finish_selection_kernel(int p, const SelState *s, const int32_t *acc, const int32_t *rej,
-                                        int32_t *sel, int32_t *filled, const GridBar *bar, int *error_flag,
+                                        int32_t *sel, int32_t *filled, const SelFlow *flow, int *error_flag,
                                         const int *skip)
 {
     if (skip && *skip) return;
-    if (bar && bar->err) {                 // a barrier of the persistent pass gave up: the selection
+    if (flow && flow->err) {               // a wait of the dataflow pass gave up: the selection
         for (int q = threadIdx.x; q < p; q += blockDim.x) sel[q] = q;   // stays valid, the error is reported
         if (threadIdx.x == 0 && error_flag) atomicOr(error_flag, 2);
         return;
@@ -419,6 +476,20 @@ __global__ void finish_selection_kernel(int p, const SelState *s, const int32_t 
 }
 
 // ---- parent matching (Sec. 3.5.1, Alg. 5) ---------------------------------------
+struct KeepNear {
+    int thr[4], ri[4], cj[4], p;
+    bool rv[4];
+    __device__ __forceinline__ bool operator()(const int (&acc)[4][4]) const
+    {
+        bool k = false;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) k |= rv[a] && cj[c] < p && cj[c] != ri[a] && acc[a][c] <= thr[a];
+        return k;
+    }
+};
+
 template <int NB>
 __global__ void __launch_bounds__(256) matching_kernel(const DevInst I, const uint32_t *planes, int p,
                                                        const uint32_t *uid, uint32_t *tested,
@@ -444,8 +515,25 @@ __global__ void __launch_bounds__(256) matching_kernel(const DevInst I, const ui
         __syncthreads();
         if (threadIdx.x < kTile) cb[threadIdx.x] = (c0 + threadIdx.x) < p ? c0 + (int)threadIdx.x : -1;
         __syncthreads();
+        // a pair can still change row i's result only if its distance is at most
+        // the best allowed distance of row i so far (ties go to the lower j; the
+        // plain best is never above the allowed one): the tile stops counting
+        // once no pair can, so every distance that is compared below the row's
+        // best is exact
+        KeepNear keep;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            uint32_t b = ballow[a];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(FULL, b, o));
+            keep.thr[a] = (int)(b >> 16);             // 0xffff while row i has no allowed partner yet
+            keep.rv[a] = r0 + 4 * ty + a < p;
+            keep.cj[a] = c0 + 4 * tx + a;
+            keep.ri[a] = r0 + 4 * ty + a;
+        }
+        keep.p = p;
         int acc[4][4];
-        tile_distances<NB>(planes, planes, I.nw, ra, cb, sm, acc);
+        tile_distances<NB, true>(planes, planes, I.nw, ra, cb, sm, acc, keep);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int i = r0 + 4 * ty + a;
@@ -602,37 +690,25 @@ cudaError_t launch_distance_matrix(const DevInst &I, const uint32_t *planesA, in
 }
 
 template <int NB>
-static cudaError_t launch_select(const DevInst &I, int m, int p, int gamma, const PopScratch &ps, const int *skip,
-                                 cudaStream_t st, bool *launched)
+static cudaError_t launch_select_flow(const DevInst &I, int m, int p, int gamma, const PopScratch &ps,
+                                      const int *skip, cudaStream_t st)
 {
-    *launched = false;
-    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!coop) return cudaSuccess;
     const size_t dyn = sizeof(TileSmem<NB>) + sizeof(uint16_t) * kChunk * kChunk;
-    cudaError_t e = cudaFuncSetAttribute(select_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaError_t e = cudaFuncSetAttribute(select_flow_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel<NB>, 256, dyn);
-    if (e != cudaSuccess || per_sm < 1) return e;
-    // as many blocks as there are 64-candidate tiles after the first chunk, at
-    // most the resident ones
-    const int tiles = std::max(1, (m - kChunk + kTile - 1) / kTile);
-    const int blocks = std::max(1, std::min(tiles, sms * per_sm));
-    const uint32_t *planes = ps.planes_ref;
-    int m_ = m, p_ = p, g_ = gamma;
-    DevInst I_ = I;
-    const int32_t *order = ps.order;
-    int32_t *mind = ps.mind, *acc = ps.acc, *rej = ps.rej;
-    const uint16_t *Dloc = ps.Dloc;
-    SelState *sst = ps.sel_state;
-    GridBar *bar = ps.bar;
-    const int *skp = skip;
-    void *args[] = {&I_, &planes, &m_, &p_, &g_, &order, &mind, &Dloc, &acc, &rej, &sst, &bar, &skp};
-    e = cudaLaunchCooperativeKernel((const void *)select_kernel<NB>, dim3(blocks), dim3(256), args, dyn, st);
-    if (e == cudaSuccess) *launched = true;
-    return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_flow_kernel<NB>, 256, dyn);
+    if (e != cudaSuccess) return e;
+    // one block per item at most, and no more than fit on the device at once
+    // (the pass needs only one to be resident; more overlap the tile updates)
+    const int C = (m + kChunk - 1) / kChunk;
+    const long long items = (long long)C + (long long)(C - 1) * C;      // an upper bound
+    const int blocks = (int)std::max(1LL, std::min(items, (long long)sms * std::max(per_sm, 1)));
+    select_flow_kernel<NB><<<blocks, 256, dyn, st>>>(I, ps.planes_ref, m, p, gamma, ps.order, ps.mind, ps.Dloc,
+                                                     ps.acc, ps.rej, ps.sel_state, ps.flow, skip);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pop_update(const DevInst &I, int p, const uint32_t *planes, const int64_t *e,
@@ -642,29 +718,19 @@ cudaError_t launch_pop_update(const DevInst &I, int p, const uint32_t *planes, c
     const int m = 2 * p;
     PopScratch ps = ps_in;
     ps.planes_ref = planes;
+    const int nchunks = (m + kChunk - 1) / kChunk;
     cudaError_t err = cudaMemsetAsync(ps.sel_state, 0, sizeof(SelState), st);
     if (err != cudaSuccess) return err;
-    err = cudaMemsetAsync(ps.bar, 0, sizeof(GridBar), st);
+    err = cudaMemsetAsync(ps.flow, 0, sizeof(int32_t) * sel_flow_ints(nchunks), st);
     if (err != cudaSuccess) return err;
     rank_kernel<<<grid_for(m, 256), 256, 0, st>>>(e, m, ps.order, skip);
     fill_int_kernel<<<grid_for(m, 256), 256, 0, st>>>(ps.mind, m, INT_MAX, skip);
-    const int nchunks = (m + kChunk - 1) / kChunk;
     NB_DISPATCH(I.nb, (chunk_local_kernel<NBV><<<dim3(nchunks, 4), 256, 0, st>>>(I, planes, ps.order, m, ps.Dloc, skip)));
-    bool launched = false;
-    if (ps.cooperative) NB_DISPATCH(I.nb, (err = launch_select<NBV>(I, m, p, gamma, ps, skip, st, &launched)));
+    NB_DISPATCH(I.nb, (err = launch_select_flow<NBV>(I, m, p, gamma, ps, skip, st)));
     if (err != cudaSuccess) return err;
-    if (kernels) *kernels = launched ? 5 : 4 + nchunks + (nchunks - 1);
-    if (!launched) {                       // no cooperative launch: one kernel pair per chunk
-        for (int k = 0; k < nchunks; ++k) {
-            resolve_chunk_kernel<<<1, 32, 0, st>>>(k, m, p, I.nv, gamma, ps.order, ps.mind, ps.Dloc, ps.acc,
-                                                   ps.rej, ps.sel_state, skip);
-            const int rows = m - (k + 1) * kChunk;
-            if (rows > 0)
-                NB_DISPATCH(I.nb, (update_mind_kernel<NBV><<<(rows + kTile - 1) / kTile, 256, 0, st>>>(I, planes, k, m, ps.order, ps.mind, ps.acc, ps.sel_state, skip)));
-        }
-    }
-    finish_selection_kernel<<<1, 256, 0, st>>>(p, ps.sel_state, ps.acc, ps.rej, sel, filled, ps.bar,
-                                               ps.error_flag, skip);
+    finish_selection_kernel<<<1, 256, 0, st>>>(p, ps.sel_state, ps.acc, ps.rej, sel, filled,
+                                               reinterpret_cast<const SelFlow *>(ps.flow), ps.error_flag, skip);
+    if (kernels) *kernels = 5;
     return cudaGetLastError();
 }
 

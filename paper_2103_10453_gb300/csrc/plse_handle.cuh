@@ -75,8 +75,6 @@ struct plse_instance {
     plse::PopScratch step_ps;          // Alg. 4 scratch for plse_pop_update
     char *arena = nullptr;             // caller-bound device range (plse_bind_workspace), or null
     size_t arena_size = 0, arena_used = 0;
-    bool shared_device = false;        // runs beside other work (batch, server): no cooperative
-                                       // launches, which would wait for the whole device
     int *noalloc_flag = nullptr;       // check flag of the last plse_local_search_noalloc call (in
                                        // the library's fixed scratch array), read by plse_sync
     cudaEvent_t done_ev = nullptr;     // recorded after the handle's latest enqueued work

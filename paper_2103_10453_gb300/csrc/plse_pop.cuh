@@ -12,16 +12,20 @@ struct SelState {
     int nacc;             // members accepted so far
     int nrej;             // candidates rejected so far (in rank order)
     int done;             // nacc reached p
-    int chunk_acc_start;  // nacc when the current chunk started
+    int pad;
 };
 
-// barrier words of a cooperative (persistent) Alg. 4 pass
-struct GridBar {
-    unsigned count;       // blocks arrived at the current barrier
-    unsigned gen;         // barriers completed
+// dataflow words of one Alg. 4 pass (zeroed before it), followed by
+// int32 upd[chunks] (finished tile updates covering chunk k) and
+// int32 accn[chunks] (members accepted once chunk k is resolved)
+struct SelFlow {
+    unsigned next;        // next work item to claim
+    int resolved;         // chunks resolved so far
     int err;              // nonzero: a block gave up waiting
     int pad;
 };
+constexpr int kSelFlowHeader = 4;   // int32 words of SelFlow
+inline size_t sel_flow_ints(int nchunks) { return kSelFlowHeader + 2 * (size_t)nchunks; }
 
 // device scratch of Alg. 4 for populations of up to `cap_p`
 struct PopScratch {
@@ -32,11 +36,9 @@ struct PopScratch {
     int32_t *rej = nullptr;    // [2p] rejected candidates in rank order
     uint16_t *Dloc = nullptr;  // [chunks][kChunk][kChunk] chunk-local distances
     SelState *sel_state = nullptr;
-    GridBar *bar = nullptr;
+    int32_t *flow = nullptr;   // SelFlow + upd[chunks] + accn[chunks]
     const uint32_t *planes_ref = nullptr;  // set by launch_pop_update for its kernels
     int *error_flag = nullptr;             // set by the caller: a failed pass is reported here
-    bool cooperative = true;               // set by the caller: Alg. 4 in one cooperative launch
-                                           // (false: one kernel pair per chunk)
 };
 
 cudaError_t launch_planes(const DevInst &I, const uint8_t *P, int count, uint32_t *planes, cudaStream_t st);

@@ -236,7 +236,7 @@ int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p, cudaStream_t st)
     int rc;
     if ((rc = dalloc(h, ps.order, m, st)) || (rc = dalloc(h, ps.mind, m, st)) || (rc = dalloc(h, ps.acc, p, st)) ||
         (rc = dalloc(h, ps.rej, m, st)) || (rc = dalloc(h, ps.Dloc, (size_t)nchunks * kChunk * kChunk, st)) ||
-        (rc = dalloc(h, ps.sel_state, 1, st)) || (rc = dalloc(h, ps.bar, 1, st)))
+        (rc = dalloc(h, ps.sel_state, 1, st)) || (rc = dalloc(h, ps.flow, sel_flow_ints(nchunks), st)))
         return rc;
     ps.cap_p = p;
     return PLSE_OK;
@@ -245,7 +245,7 @@ int ensure_pop_scratch(plse_instance *h, PopScratch &ps, int p, cudaStream_t st)
 void free_pop_scratch(plse_instance *h, PopScratch &ps, cudaStream_t st)
 {
     h_free(h, ps.order, st); h_free(h, ps.mind, st); h_free(h, ps.acc, st); h_free(h, ps.rej, st);
-    h_free(h, ps.Dloc, st); h_free(h, ps.sel_state, st); h_free(h, ps.bar, st);
+    h_free(h, ps.Dloc, st); h_free(h, ps.sel_state, st); h_free(h, ps.flow, st);
     ps = PopScratch();
 }
 
@@ -275,7 +275,7 @@ size_t solver_bytes(const plse_instance *h, int p, int gens)
          a((size_t)I.nv) + a(4 * (size_t)gens);
     const int m = 2 * p, nchunks = (m + kChunk - 1) / kChunk;
     t += a(4 * (size_t)m) + a(4 * (size_t)m) + a(4 * (size_t)p) + a(4 * (size_t)m) +
-         a(2 * (size_t)nchunks * kChunk * kChunk) + a(sizeof(SelState)) + a(sizeof(GridBar));
+         a(2 * (size_t)nchunks * kChunk * kChunk) + a(sizeof(SelState)) + a(4 * sel_flow_ints(nchunks));
     return t;
 }
 
@@ -432,7 +432,6 @@ static int issue_generation_rest(plse_instance *h, const GenPlan &q)
     CK(cudaEventRecord(s->gev[q.slot][2], st));
     CK(launch_planes(I, q.Pp, p, s->planes[cur] + (size_t)p * stride, st));
     s->ps.error_flag = h->ws.counters ? h->ws.counters + 1 : nullptr;
-    s->ps.cooperative = !h->shared_device;
     long long sel_kernels = 0;
     CK(launch_pop_update(I, p, s->planes[cur], s->e[cur], prm.spacing_gamma, s->ps, s->sel, nullptr, skip, st,
                          &sel_kernels));

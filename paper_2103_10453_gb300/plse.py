@@ -90,7 +90,6 @@ SIGNATURES = {
     "plse_workspace_size": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "plse_bind_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
     "plse_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
-    "plse_set_shared_device": (C.c_int, [_vp, C.c_int]),
     "plse_run_timeline": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.POINTER(C.c_float)]),
     "plse_default_params": (None, [C.POINTER(Params)]),
     "plse_set_params": (C.c_int, [_vp, C.POINTER(Params)]),
@@ -238,11 +237,6 @@ class Instance:
         return l.value, w.value, c.value, r.value
 
     # ---- caller-supplied device memory ------------------------------------
-    def set_shared_device(self, shared=True):
-        """plse_set_shared_device: the handle's runs share the GPU with other
-        concurrent work (Alg. 4 as per-chunk kernels, not one cooperative launch)."""
-        self._check(self.lib.plse_set_shared_device(self.h, 1 if shared else 0))
-
     def workspace_size(self, pop: int, max_generations: int) -> int:
         """Device bytes a run of ``pop`` individuals and ``max_generations``
         generations takes (plse_workspace_size)."""

@@ -76,19 +76,17 @@ def test_issue_query_loop_equals_blocking_run(plse):
 
 
 def test_concurrent_runs_on_streams_equal_runs_alone(plse):
-    """Several runs driven by plse_run_issue on their own streams at once, with
-    and without plse_set_shared_device (per-chunk Alg. 4 kernels instead of the
-    cooperative launch), give each run's result alone; the population is large
-    enough for several Alg. 4 chunks."""
+    """Several runs driven by plse_run_issue on their own streams at once give
+    each run's result alone; the populations are large enough for several
+    Alg. 4 chunks, whose dataflow passes then share the GPU."""
     import torch
     gs = grids()[:3]
     jobs = [(300, 4, 150, 7), (260, 3, 120, 8), (200, 4, 100, 9)]
     refs = [alone(plse, g, j) for g, j in zip(gs, jobs)]
-    for shared in (False, True):
+    for _ in range(2):
         insts, streams = [], []
         for g, (pop, gens, iters, seed) in zip(gs, jobs):
             G = plse.Instance(g)
-            G.set_shared_device(shared)
             s = torch.cuda.Stream()
             G.run_begin(pop, gens, iters, seed, stream=s)
             insts.append(G)
