@@ -779,11 +779,13 @@ def run_pop_sweep(args):
 def run_lsc_case(args):
     """Latin square completion (App. B): cyclic-delete instances, which have a
     complete square as witness, two per (n, r) with n in {50, 60, 70} and
-    r in {0.3, ..., 0.8} (seeds 7000 + k); population --batch-pop, at most
-    --generations generations, phase-1 iterations 10|V|, optimality stop on.
-    Solved fraction, generations and device time to the complete square."""
+    r in {0.3, ..., 0.8} (seeds 7000 + k); population --batch-pop (default
+    1024), at most --generations generations, phase-1 iterations 10|V|,
+    optimality stop on.  Solved fraction, generations and device time to the
+    complete square."""
     import numpy as np
     from paper_2103_10453_gb300 import inputs, plse
+    pop = args.batch_pop or 1024
     rows, k = [], 0
     for n in (50, 60, 70):
         for r in (0.3, 0.4, 0.5, 0.6, 0.7, 0.8):
@@ -791,14 +793,14 @@ def run_lsc_case(args):
                 grid = inputs.cyclic_delete(n, r, 7000 + k)[0]
                 k += 1
                 G = plse.Instance(grid)
-                res = G.solve(args.batch_pop, args.generations, 10 * G.nv, 1, with_stats=True)
+                res = G.solve(pop, args.generations, 10 * G.nv, 1, with_stats=True)
                 rows.append({"n": n, "r": r, "solved": res["score"] == n * n,
                              "generations": res["generations"], "ms": round(res["ms_total"], 1)})
                 G.close()
     solved = [x for x in rows if x["solved"]]
     ms = np.array([x["ms"] for x in solved]) if solved else np.zeros(1)
     print(json.dumps({"case": "lsc", "instances": len(rows), "solved": len(solved),
-                      "population": args.batch_pop, "max_generations": args.generations,
+                      "population": pop, "max_generations": args.generations,
                       "ms_to_solve": {"p50": round(float(np.percentile(ms, 50)), 1),
                                       "p90": round(float(np.percentile(ms, 90)), 1),
                                       "max": round(float(ms.max()), 1)},

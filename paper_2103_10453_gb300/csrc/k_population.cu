@@ -476,20 +476,6 @@ __global__ void finish_selection_kernel(int p, const SelState *s, const int32_t 
 }
 
 // ---- parent matching (Sec. 3.5.1, Alg. 5) ---------------------------------------
-struct KeepNear {
-    int thr[4], ri[4], cj[4], p;
-    bool rv[4];
-    __device__ __forceinline__ bool operator()(const int (&acc)[4][4]) const
-    {
-        bool k = false;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) k |= rv[a] && cj[c] < p && cj[c] != ri[a] && acc[a][c] <= thr[a];
-        return k;
-    }
-};
-
 template <int NB>
 __global__ void __launch_bounds__(256) matching_kernel(const DevInst I, const uint32_t *planes, int p,
                                                        const uint32_t *uid, uint32_t *tested,
@@ -515,25 +501,8 @@ __global__ void __launch_bounds__(256) matching_kernel(const DevInst I, const ui
         __syncthreads();
         if (threadIdx.x < kTile) cb[threadIdx.x] = (c0 + threadIdx.x) < p ? c0 + (int)threadIdx.x : -1;
         __syncthreads();
-        // a pair can still change row i's result only if its distance is at most
-        // the best allowed distance of row i so far (ties go to the lower j; the
-        // plain best is never above the allowed one): the tile stops counting
-        // once no pair can, so every distance that is compared below the row's
-        // best is exact
-        KeepNear keep;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            uint32_t b = ballow[a];
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(FULL, b, o));
-            keep.thr[a] = (int)(b >> 16);             // 0xffff while row i has no allowed partner yet
-            keep.rv[a] = r0 + 4 * ty + a < p;
-            keep.cj[a] = c0 + 4 * tx + a;
-            keep.ri[a] = r0 + 4 * ty + a;
-        }
-        keep.p = p;
         int acc[4][4];
-        tile_distances<NB, true>(planes, planes, I.nw, ra, cb, sm, acc, keep);
+        tile_distances<NB>(planes, planes, I.nw, ra, cb, sm, acc);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int i = r0 + 4 * ty + a;
