@@ -116,6 +116,22 @@ LSLaunch plan_local_search_multi(const DevInst *insts, int count, int device, in
 // each job's scratch must hold L.slots() walk slots.
 cudaError_t launch_local_search_multi(const LSJob *jobs, int njobs, const LSLaunch &L, cudaStream_t st);
 
+// Launch entry points of the local-search kernels of one colour-word class
+// (NWC = 32-colour words, 1..4); each class is instantiated in its own
+// translation unit (k_ls_w1.cu .. k_ls_w4.cu).
+template <int NWC>
+struct LSKernels {
+    static cudaError_t launch(const DevInst &I, const LSArgs &a, const LSLaunch &L, cudaStream_t st);
+    // sets the block's shared-memory size; returns resident blocks per SM
+    static int set_smem(int group, size_t smem, int threads);
+    static cudaError_t launch_multi(const LSJob *jobs, int njobs, const LSLaunch &L, cudaStream_t st);
+    static int set_smem_multi(int group, size_t smem, int threads);
+};
+extern template struct LSKernels<1>;
+extern template struct LSKernels<2>;
+extern template struct LSKernels<3>;
+extern template struct LSKernels<4>;
+
 // 32-colour words of a colour mask over colours 0..n
 __host__ __device__ inline int colour_words(int n) { return n < 32 ? 1 : n < 64 ? 2 : n < 96 ? 3 : 4; }
 
