@@ -51,7 +51,8 @@ typedef struct {
     int32_t tenure_rand;           /* L uniform in [0, tenure_rand) = [0, 9]     */
     int32_t phase1_phi2;           /* 2*phi of phase 1 (phi = 0.5 -> 1)          */
     int32_t phase2_phi2_per_v;     /* 2*phi of phase 2 per |V| (phi = |V| -> 2)  */
-    int32_t phase2_iter_per_v;     /* phase-2 iterations per |V| (2)             */
+    int32_t phase2_iter_per_v;     /* phase-2 iterations per |V| (2); at most    */
+                                   /* 2^30 iterations in all (else PLSE_ENOTSUP) */
     int32_t spacing_gamma;         /* Alg. 4 spacing D > |V|/gamma (10)          */
     int32_t beta;                  /* AUX parameter beta (20)                    */
     int32_t mode;                  /* PLSE_MODE_PLITS, _PARTIALCOL or _AUTO      */

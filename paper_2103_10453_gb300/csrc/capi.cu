@@ -191,6 +191,8 @@ int check_exactness(plse_instance *h, const plse_params &p)
     const long long phi2 = std::max<long long>(p.phase1_phi2, (long long)p.phase2_phi2_per_v * nv);
     if (phi2 * 2 * (n > 0 ? n - 1 : 0) + 2 > kMaxD2)
         return fail(h, PLSE_ENOTSUP, "penalty too large for exact 2dF keys");
+    if ((long long)p.phase2_iter_per_v * nv > (1ll << 30))   // the walks count iterations in 32 bits
+        return fail(h, PLSE_ENOTSUP, "phase-2 iterations %lld exceed 2^30", (long long)p.phase2_iter_per_v * nv);
     return PLSE_OK;
 }
 

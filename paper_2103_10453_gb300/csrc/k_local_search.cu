@@ -57,7 +57,7 @@ LSLaunch plan_local_search(const DevInst &I, int device, int count, int group, i
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     // one block per SM holding as many walk slots as fit (at most the kernel's
-    // thread limit: 512 for 64 <= n < 96, 384 from 96, 256 below 64 with two
+    // thread limit: 640 for 64 <= n < 96, 384 from 96, 256 below 64 with two
     // blocks); the colouring stays in the slot unless that would cut the walks
     long long by_threads = std::max(1, max_threads_for(L.colour_words) / L.group);
     if (max_walks > 0) by_threads = std::min<long long>(by_threads, max_walks);

@@ -71,11 +71,12 @@ __device__ __forceinline__ int tenure_div(const LSArgs &a, int x)
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// threads per block of the local search: one block per SM at n >= 64 (512
-// threads for n < 96, 384 from 96, whose kernel needs more registers), two
-// blocks of 256 per SM below.  The register budget per thread follows from it.
+// threads per block of the local search: one block per SM at n >= 64 (640
+// threads, 20 one-warp walks, for n < 96 at 95 registers without spills; 384
+// from 96, whose kernel needs more registers), two blocks of 256 per SM below.
+// The register budget per thread follows from it.
 #ifndef PLSE_LS_THREADS_N64
-#define PLSE_LS_THREADS_N64 512
+#define PLSE_LS_THREADS_N64 640
 #endif
 template <int NWC>
 constexpr int kMaxThreads = NWC == 3 ? PLSE_LS_THREADS_N64 : NWC == 4 ? 384 : 256;
@@ -106,7 +107,7 @@ __host__ __device__ inline SmemPlan make_plan(const DevInst &I, int warps, bool 
     p.off_cmask = o;  o += 4 * (size_t)I.nw;
     p.off_lmask = o;  o += 4 * (size_t)I.nw;
     p.off_red = align16(o);
-    o = p.off_red + 8 * 2 * (size_t)warps + 4 * 2 * (size_t)warps + 4 * 16;
+    o = p.off_red + 8 * 2 * (size_t)warps + 4 * 2 * (size_t)warps + 4 * 32;
     p.slot = align16(o);
     return p;
 }
@@ -125,8 +126,9 @@ struct Slot {
                                 // x = e0 | e1 << 16, y = c0 | c1 << 8 | emax << 16
     unsigned long long *red;    // [2][NW] best key per warp (double-buffered)
     int *red_cnt;               // [2][NW] live candidates seen per warp
-    int *scal;                  // [16]: 0 list length, 2 counts >= 4, 4 |C(S)|, 5..6 move
-                                // scratch, 7 walk id, 8.. reductions
+    int *scal;                  // [32]: 0 list length, 2 counts >= 4, 4 |C(S)|, 5..6 move
+                                // scratch, 7 walk id, 8..15 reductions, 16..29 the walk's
+                                // 64-bit work totals (WalkTotals)
 };
 
 // Per-thread view: instance data, its slot and its place in the group.
@@ -153,8 +155,9 @@ __device__ __forceinline__ void gsync(const Ctx &c)
 }
 
 // context of thread threadIdx.x in group g: instance data at rc / allow /
-// linelen (shared or global memory), the walk's slot at sb
-template <int GT>
+// linelen (shared or global memory), the walk's slot at sb; NWC = colour words
+// of the instance (a compile-time constant of the kernel)
+template <int NWC, int GT>
 __device__ __forceinline__ Ctx make_ctx_at(const DevInst &I, bool s_smem, const uint16_t *rc, const uint4 *allow,
                                            const uint8_t *linelen, uint8_t *sb)
 {
@@ -182,24 +185,43 @@ __device__ __forceinline__ Ctx make_ctx_at(const DevInst &I, bool s_smem, const 
     c.s.red_cnt = reinterpret_cast<int *>(sb + p.off_red + 16 * Grp<GT>::NW);
     c.s.scal = c.s.red_cnt + 2 * Grp<GT>::NW;
     c.n = I.n;
-    c.cw = colour_words(I.n);
+    c.cw = NWC;
     return c;
 }
 
 // block layout of the single-instance kernel: instance part, then the slots
-template <int GT>
+template <int NWC, int GT>
 __device__ __forceinline__ Ctx make_ctx(uint8_t *base, const DevInst &I, bool s_smem)
 {
     const SmemPlan p = make_plan(I, Grp<GT>::NW, s_smem);
     const int g = threadIdx.x / GT;
-    return make_ctx_at<GT>(I, s_smem, reinterpret_cast<const uint16_t *>(base),
+    return make_ctx_at<NWC, GT>(I, s_smem, reinterpret_cast<const uint16_t *>(base),
                            reinterpret_cast<const uint4 *>(base + align16(2 * (size_t)I.nv)),
                            base + align16(2 * (size_t)I.nv) + 32 * (size_t)I.n, base + p.inst + p.slot * g);
 }
 
-struct LaneStats {
+// Work counters of a walk (plse_walk_stats), kept as 64-bit totals in the
+// slot's shared memory.  Iterations and moves are added per phase from the
+// iteration count (a move is counted unless the iteration had none).  The sums
+// that grow every iteration are 32-bit registers (the scanned pairs per lane),
+// folded into the totals every 2^14 iterations and at the end of each phase,
+// which keeps them below 2^32 at any instance size (fewer than 2^14 candidates
+// of at most 127 colours per iteration).  After a failed device check the
+// counters are unspecified.
+struct WalkTotals {
     long long iterations, moves, cand, pairs, deg, improvements, uncolored;
 };
+
+struct IterCounters {
+    uint32_t cand, pairs, deg;
+};
+
+constexpr int kFoldMask = (1 << 14) - 1;
+
+__device__ __forceinline__ WalkTotals *walk_totals(const Ctx &c)
+{
+    return reinterpret_cast<WalkTotals *>(c.s.scal + 16);
+}
 
 template <int GT>
 __device__ __forceinline__ int gsum(int x, const Ctx &c)
@@ -245,6 +267,32 @@ __device__ __forceinline__ long long gsum64(long long x, const Ctx &c)
     for (int k = 0; k < Grp<GT>::NW; ++k) t += (long long)c.s.red[k];
     gsync<GT>(c);
     return t;
+}
+
+// adds the iteration counters to the walk's totals and clears them (the whole
+// group calls it)
+template <int GT>
+__device__ __forceinline__ void fold_counters(const Ctx &c, IterCounters &k)
+{
+    const long long pairs = gsum64<GT>((long long)k.pairs, c);
+    if (c.gt == 0) {
+        WalkTotals *w = walk_totals(c);
+        w->cand += k.cand;
+        w->pairs += pairs;
+        w->deg += k.deg;
+    }
+    k = IterCounters{0u, 0u, 0u};
+}
+
+// iterations 1 .. t-1 of a phase were executed; every one of them made a move
+// unless it was counted off when it had none
+__device__ __forceinline__ void count_iterations(const Ctx &c, int t)
+{
+    if (c.gt == 0) {
+        WalkTotals *w = walk_totals(c);
+        w->iterations += t - 1;
+        w->moves += t - 1;
+    }
 }
 
 template <int GT>
@@ -561,51 +609,6 @@ __device__ __forceinline__ int first_bit(const uint32_t (&set)[NWC])
     return jb;
 }
 
-// min over colours j in m of s_j (lowest j on ties) by most-significant-plane-
-// first elimination over the 8 planes of s, in straight-line code; planes 3..7
-// are skipped when no colour of the word set reaches 8; -1 if m is empty
-template <int NWC>
-__device__ __forceinline__ int bits_min(const uint32_t (&s)[NWC][8], const uint32_t (&m)[NWC], int &smin)
-{
-    uint32_t set[NWC], hi = 0;
-#pragma unroll
-    for (int q = 0; q < NWC; ++q) {
-        set[q] = m[q];
-        hi |= s[q][3] | s[q][4] | s[q][5] | s[q][6] | s[q][7];
-    }
-    uint32_t val = 0;
-    if (hi) {
-#pragma unroll
-        for (int p = 7; p >= 3; --p) {
-            uint32_t t[NWC], anyt = 0;
-#pragma unroll
-            for (int q = 0; q < NWC; ++q) {
-                t[q] = set[q] & ~s[q][p];
-                anyt |= t[q];
-            }
-            const bool keep = anyt != 0u;
-#pragma unroll
-            for (int q = 0; q < NWC; ++q) set[q] = keep ? t[q] : set[q];
-            val |= keep ? 0u : (1u << p);
-        }
-    }
-#pragma unroll
-    for (int p = 2; p >= 0; --p) {
-        uint32_t t[NWC], anyt = 0;
-#pragma unroll
-        for (int q = 0; q < NWC; ++q) {
-            t[q] = set[q] & ~s[q][p];
-            anyt |= t[q];
-        }
-        const bool keep = anyt != 0u;
-#pragma unroll
-        for (int q = 0; q < NWC; ++q) set[q] = keep ? t[q] : set[q];
-        val |= keep ? 0u : (1u << p);
-    }
-    smin = (int)val;
-    return first_bit<NWC>(set);
-}
-
 // Best admissible move of candidate v as key 2dF*256 + j (INT_MAX: none).
 //   v uncoloured:  2dF(j) = base_unc + mult*s_j        (j != 0)
 //   v coloured i:  2dF(j) = mult*(s_j - g_i)            (j != 0, j != i)
@@ -670,7 +673,8 @@ struct TabuView {
     uint32_t e0, e1, c0, c1;
     bool gslow;                 // an evicted entry may be live: colours outside the cache go to G
     uint32_t tabs;              // absolute clock of this iteration
-    const uint32_t *Gv;         // G row of v
+    const uint32_t *G;          // the slot's table
+    uint32_t row;               // v * n1p: G row of v (addressed only on a lookup)
 };
 
 __device__ __forceinline__ TabuView tabu_view(const DevInst &I, const uint2 &te, const Clock &ck, uint32_t trel,
@@ -683,7 +687,8 @@ __device__ __forceinline__ TabuView tabu_view(const DevInst &I, const uint2 &te,
     t.c1 = (te.y >> 8) & 0xFFu;
     t.gslow = (te.y >> 16) >= trel;
     t.tabs = ck.base + ck.shift + trel;
-    t.Gv = G + (size_t)v * I.n1p;
+    t.G = G;
+    t.row = (uint32_t)v * (uint32_t)I.n1p;
     return t;
 }
 
@@ -695,19 +700,28 @@ __device__ __forceinline__ int eval_special(const TabuView &tv, uint32_t trel, i
 {
     int best = INT_MAX;
     if (i != 0) {
-        const bool tabu0 = tv.c0 == 0u ? tv.e0 >= trel : tv.c1 == 0u ? tv.e1 >= trel : (tv.gslow && tv.Gv[0] >= tv.tabs);
+        const bool tabu0 = tv.c0 == 0u ? tv.e0 >= trel : tv.c1 == 0u ? tv.e1 >= trel : (tv.gslow && tv.G[tv.row] >= tv.tabs);
         if (!tabu0 || d2zero < A) best = d2zero * kKeyScale;
     }
+    // the live cache colours of m (an expired one stays in m as an ordinary
+    // colour); a live one is tabu and admissible by aspiration only, which needs
+    // 2dF < A, while 2dF >= base2 for every colour (s_j >= 0): the values are
+    // needed only when base2 < A
+    const bool l0 = tv.c0 != 0u && tv.e0 >= trel && test_bit<NWC>(m, tv.c0);
+    const bool l1 = tv.c1 != 0u && tv.e1 >= trel && test_bit<NWC>(m, tv.c1);
+    if ((l0 || l1) && base2 < A) {
 #pragma unroll
-    for (int sx = 0; sx < 2; ++sx) {
-        const uint32_t cs = sx ? tv.c1 : tv.c0, es = sx ? tv.e1 : tv.e0;
-        // an expired cache colour stays in m as an ordinary colour
-        if (cs != 0u && cs < 128u && es >= trel && test_bit<NWC>(m, cs)) {
-            clear_bit<NWC>(m, cs);
-            const int d2 = base2 + mult * sval(cs);
-            if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
+        for (int sx = 0; sx < 2; ++sx) {
+            const uint32_t cs = sx ? tv.c1 : tv.c0;
+            if (sx ? l1 : l0) {
+                const int d2 = base2 + mult * sval(cs);
+                if (d2 < A) best = min(best, d2 * kKeyScale + (int)cs);
+            }
         }
     }
+    // out of m (a colour >= 128 clears nothing)
+    clear_bit<NWC>(m, l0 ? tv.c0 : 255u);
+    clear_bit<NWC>(m, l1 ? tv.c1 : 255u);
     return best;
 }
 
@@ -735,7 +749,12 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
         s1[q] = x1 ^ cy;
         s2[q] = (ra.y & ka.y) | (cy & x1);
     }
-    const int gi = i ? value3<NWC>(s0, s1, s2, (uint32_t)i) - 2 : 0;
+    // gamma[v][i] from the row and column words of colour i (counts <= 3 here)
+    const uint2 ri = Pr[i >> 5], ki = Pc[i >> 5];
+    const uint32_t bi = (uint32_t)i & 31u;
+    const int gi = i ? (int)(((ri.x >> bi) & 1u) + ((ri.y >> bi) & 1u) * 2u + ((ki.x >> bi) & 1u) +
+                             ((ki.y >> bi) & 1u) * 2u) - 2
+                     : 0;
     const int base2 = i ? -mult * gi : base_unc;
     const int d2zero = 2 - mult * gi;
     const uint4 ar = c.allow[r], ac = c.allow[I.n + cc];
@@ -757,7 +776,7 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
         const int jb = bits_min3<NWC>(s0, s1, s2, m, smin);
         if (jb < 0) break;
         const int d2 = base2 + mult * smin;
-        const bool tabu = tv.gslow && (uint32_t)jb != tv.c0 && (uint32_t)jb != tv.c1 && tv.Gv[jb] >= tv.tabs;
+        const bool tabu = tv.gslow && (uint32_t)jb != tv.c0 && (uint32_t)jb != tv.c1 && tv.G[tv.row + (uint32_t)jb] >= tv.tabs;
         if (!tabu || d2 < A) {
             best = min(best, d2 * kKeyScale + jb);
             break;
@@ -765,6 +784,68 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
         clear_bit<NWC>(m, (uint32_t)jb);
     }
     return best;
+}
+
+// s_j = R[line_r][j] + K[line_c][j] for the 32 colours of word q, bit-sliced
+// (8 planes; planes 2..6 of a line read from global memory only when one of its
+// counts in the word is >= 4)
+__device__ __forceinline__ void word_sum(const Ctx &c, int rl, int cl, int q, uint32_t (&s)[8])
+{
+    const size_t wr = plane_word(c, rl, q * 32), wc = plane_word(c, cl, q * 32);
+    const uint2 r0 = c.s.P01[wr];
+    const uint2 k0 = c.s.P01[wc];
+    uint32_t a[7] = {r0.x, r0.y, 0u, 0u, 0u, 0u, 0u};
+    uint32_t b[7] = {k0.x, k0.y, 0u, 0u, 0u, 0u, 0u};
+    if (c.s.PH[wr]) {
+        const uint32_t *g = c.s.HP + wr * kHi;
+#pragma unroll
+        for (int p = 0; p < 5; ++p) a[p + 2] = g[p];
+    }
+    if (c.s.PH[wc]) {
+        const uint32_t *g = c.s.HP + wc * kHi;
+#pragma unroll
+        for (int p = 0; p < 5; ++p) b[p + 2] = g[p];
+    }
+    uint32_t carry = 0u;
+#pragma unroll
+    for (int p = 0; p < 7; ++p) {
+        const uint32_t x = a[p] ^ b[p];
+        s[p] = x ^ carry;
+        carry = (a[p] & b[p]) | (carry & x);
+    }
+    s[7] = carry;
+}
+
+// min over the colours j of m of s_j (lowest j on ties) with exact counts, one
+// colour word at a time: each word's minimum by most-significant-plane-first
+// elimination over its 8 planes, then the smallest (value, word); -1 if m is
+// empty.  Only one word's planes are held at once.
+template <int NWC>
+__device__ __forceinline__ int exact_min(const Ctx &c, int rl, int cl, const uint32_t (&m)[NWC], int &smin)
+{
+    uint32_t bestv = 0xFFFFFFFFu;
+    int jb = -1;
+#pragma unroll 1
+    for (int q = 0; q < NWC; ++q) {                 // not unrolled: one word's planes live at a time
+        uint32_t mq = m[0];
+#pragma unroll
+        for (int w = 1; w < NWC; ++w) mq = q == w ? m[w] : mq;
+        uint32_t s[8];
+        word_sum(c, rl, cl, q, s);
+        uint32_t set = mq, val = 0u;
+#pragma unroll
+        for (int p = 7; p >= 0; --p) {
+            const uint32_t t = set & ~s[p];
+            const bool keep = t != 0u;                  // some colour of the word has bit p clear
+            set = keep ? t : set;
+            val |= keep ? 0u : (1u << p);
+        }
+        const bool better = mq != 0u && val < bestv;    // strict: a lower word wins ties
+        bestv = better ? val : bestv;
+        jb = better ? q * 32 + __ffs(set) - 1 : jb;
+    }
+    smin = (int)bestv;
+    return jb;
 }
 
 // eval with exact counts (planes 2..6 read where a count reaches 4)
@@ -777,33 +858,6 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
     iv = i;
     const uint16_t rc = c.rc[v];
     const int r = rc >> 8, cc = rc & 255, rl = r, cl = I.n + cc;
-    // s = R[r] + K[c] for every colour, bit-sliced
-    uint32_t s[NWC][8];
-#pragma unroll
-    for (int q = 0; q < NWC; ++q) {
-        const uint2 r0 = c.s.P01[(size_t)rl * NWC + q];
-        const uint2 k0 = c.s.P01[(size_t)cl * NWC + q];
-        uint32_t a[7] = {r0.x, r0.y, 0u, 0u, 0u, 0u, 0u};
-        uint32_t b[7] = {k0.x, k0.y, 0u, 0u, 0u, 0u, 0u};
-        if (c.s.PH[(size_t)rl * NWC + q]) {
-            const uint32_t *g = c.s.HP + ((size_t)rl * NWC + q) * kHi;
-#pragma unroll
-            for (int p = 0; p < 5; ++p) a[p + 2] = g[p];
-        }
-        if (c.s.PH[(size_t)cl * NWC + q]) {
-            const uint32_t *g = c.s.HP + ((size_t)cl * NWC + q) * kHi;
-#pragma unroll
-            for (int p = 0; p < 5; ++p) b[p + 2] = g[p];
-        }
-        uint32_t carry = 0u;
-#pragma unroll
-        for (int p = 0; p < 7; ++p) {
-            const uint32_t x = a[p] ^ b[p];
-            s[q][p] = x ^ carry;
-            carry = (a[p] & b[p]) | (carry & x);
-        }
-        s[q][7] = carry;
-    }
     const int gi = i ? count_of(c, rl, i) + count_of(c, cl, i) - 2 : 0;
     const int base2 = i ? -mult * gi : base_unc;
     const int d2zero = 2 - mult * gi;
@@ -823,10 +877,10 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
                                  [&](uint32_t k) { return count_of(c, rl, (int)k) + count_of(c, cl, (int)k); });
     for (;;) {
         int smin = 0;
-        const int jb = bits_min<NWC>(s, m, smin);
+        const int jb = exact_min<NWC>(c, rl, cl, m, smin);
         if (jb < 0) break;
         const int d2 = base2 + mult * smin;
-        const bool tabu = tv.gslow && (uint32_t)jb != tv.c0 && (uint32_t)jb != tv.c1 && tv.Gv[jb] >= tv.tabs;
+        const bool tabu = tv.gslow && (uint32_t)jb != tv.c0 && (uint32_t)jb != tv.c1 && tv.G[tv.row + (uint32_t)jb] >= tv.tabs;
         if (!tabu || d2 < A) {
             best = min(best, d2 * kKeyScale + jb);
             break;
@@ -949,7 +1003,7 @@ __device__ __forceinline__ int list_pass(const Ctx &c, int base, int len, int &w
 // and stay in registers; wider groups pass them through the slot's scalars.
 template <int NWC, int GT>
 __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, const Ctx &c, uint32_t *G, uint8_t *gbest,
-                            int slot, int ind, int phase, int64_t N, int phi2, int span, LaneStats &st,
+                            int slot, int ind, int phase, int64_t N, int phi2, int span,
                             long long &F2best_out)
 {
     constexpr int W = Grp<GT>::W, NW = Grp<GT>::NW;
@@ -964,11 +1018,14 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
     int len = rebuild_list<GT>(I, c);
     Clock ck = claim_clock<GT>(I, a, c, G, slot, span);
 
-    const uint32_t ctr2 = ((uint32_t)a.gen << 8) | (kPurposeTabu << 4) | (uint32_t)phase;
     uint32_t Lr = 0, rotr = 0;
     bool ok = true;
-    for (long long t = 1; t <= N; ++t) {
+    IterCounters wc = {0u, 0u, 0u};
+    const int Nt = (int)N;                               // at most 2^30 (checked by the host)
+    int t = 1;
+    for (; t <= Nt; ++t) {
         if (f + nconf == 0) break;                       // nothing left to improve
+        if ((t & kFoldMask) == 0) fold_counters<GT>(c, wc);
         uint32_t trel = (uint32_t)(t - ck.shift);
         if (trel >= kRebaseAt) {
             gsync<GT>(c);
@@ -984,6 +1041,8 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         if (len > 2 * (f + nconf) + 64) len = rebuild_list<GT>(I, c);
         const int q = (int)((t - 1) & (W - 1));
         if (q == 0) {
+            // counter (iteration, individual, gen << 8 | purpose << 4 | phase)
+            const uint32_t ctr2 = ((uint32_t)a.gen << 8) | (kPurposeTabu << 4) | (uint32_t)phase;
             const uint4 u = philox4x32_10(make_uint4((uint32_t)(t + c.gl), (uint32_t)ind, ctr2, 0u), a.key0, a.key1);
             Lr = bounded(u.x, (uint32_t)a.tenure_rand);
             rotr = bounded(u.y, (uint32_t)I.nv);
@@ -1001,7 +1060,7 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             int pairs, iv;
             const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs, iv)
                                : eval_vertex<NWC>(I, c, G, ck, trel, v, phi2, -2, A, pairs, iv);
-            st.pairs += pairs;
+            wc.pairs += (uint32_t)pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, iv));
         };
         if constexpr (NW == 1) {
@@ -1020,9 +1079,11 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         int ncand;
         const unsigned long long best = group_best<GT>(c, (int)(t & 1), key, live, ncand);
         if (ncand != f + nconf) { ok = false; break; }
-        st.iterations += 1;
-        st.cand += ncand;
-        if (best == kNoKey) continue;                    // every move tabu
+        wc.cand += (uint32_t)ncand;
+        if (best == kNoKey) {                            // every move tabu
+            if (c.gt == 0) walk_totals(c)->moves -= 1;
+            continue;
+        }
 
         const uint32_t bhi = (uint32_t)(best >> 32), blo = (uint32_t)best;
         const int d2 = (int)bhi - (1 << 30);
@@ -1061,21 +1122,24 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             if (c.gl == 0) c.s.S[v] = (uint8_t)j;
             if (c.gl < 4 && xk) c.s.xr[xidx] = (uint16_t)(xold ^ v);   // v leaves i, joins j
             const int dh_tot = __reduce_add_sync(c.gm, dh);
-            // counts of colours i and j on the moved row and column, after the move
-            const int Ri = __shfl_sync(c.gm, cnt_i, 0, W), Ki = __shfl_sync(c.gm, cnt_i, 1, W);
-            const int Rj = __shfl_sync(c.gm, cnt_j, 0, W), Kj = __shfl_sync(c.gm, cnt_j, 1, W);
+            // counts of colours i and j on the moved row (lane 0) and column (lane 1)
+            // after the move, packed i | j << 8: lane l reads line l & 1's, and lane
+            // 0 also the column's
+            const int packed = cnt_i | (cnt_j << 8);
+            const int line_cnt = __shfl_sync(c.gm, packed, c.gl & 1, W);
+            const int col_cnt = __shfl_xor_sync(c.gm, packed, 1, W);
             __syncwarp(c.gm);
             // The mates whose conflict status can change, one per (line, colour) at
             // most: the only other holder of colour i (count after the move 1) and
             // the other holder of colour j (count after 2).  Each is read from the
-            // member-id XOR of its line: lane 0 row/i, 1 column/i, 2 row/j, 3 column/j.
+            // member-id XOR of its line: lane 0 row/i, 1 column/i, 2 row/j, 3 column/j
+            // (colour xk, line xline).
             int dconf = 0;
-            int u = -1, su = 0, cl = 0;
+            const int su = xk;
+            const int cl = c.gl < 2 ? 1 : 2;              // the mate's count on that line
+            const int cnt_l = c.gl < 2 ? (line_cnt & 255) : (line_cnt >> 8);
+            const int u = (c.gl < 4 && xk && cnt_l == cl) ? (c.gl < 2 ? xold ^ v : xold) : -1;
             const bool row_mate = (c.gl & 1) == 0;
-            if (c.gl == 0 && i && Ri == 1) { u = xold ^ v; su = i; cl = Ri; }   // the last holder of i
-            if (c.gl == 1 && i && Ki == 1) { u = xold ^ v; su = i; cl = Ki; }
-            if (c.gl == 2 && j && Rj == 2) { u = xold; su = j; cl = Rj; }       // the other holder of j
-            if (c.gl == 3 && j && Kj == 2) { u = xold; su = j; cl = Kj; }
             bool want = false, bad_mate = false;
             if (u >= 0) {
                 if (u >= I.nv || u == v || c.s.S[u] != su) {
@@ -1095,7 +1159,7 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             list_append(c, want, u, len);
             bad = __any_sync(c.gm, bad_mate);
             if (c.gl == 0) {
-                const int newc = j ? (int)(Rj + Kj - 2 > 0) : 0;
+                const int newc = j ? (int)(cnt_j + (col_cnt >> 8) - 2 > 0) : 0;   // v's own status at j
                 if (j != 0 && !newc) atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
                 dconf += newc - (i != 0 ? 1 : 0);
             }
@@ -1121,14 +1185,15 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             nconf = c.s.scal[4];
         }
         if (bad) { ok = false; break; }
-        st.moves += 1;
-        if (c.gt == 0) st.deg += vertex_degree(I, c, v);
+        if (c.gt == 0) wc.deg += (uint32_t)vertex_degree(I, c, v);
         if (F2 < F2best) {
             F2best = F2;
-            st.improvements += 1;
+            if (c.gt == 0) walk_totals(c)->improvements += 1;
             gcopy<GT>(gbest, c.s.S, I.nv, c);
         }
     }
+    fold_counters<GT>(c, wc);
+    count_iterations(c, t);
     gsync<GT>(c);
     gcopy<GT>(c.s.S, gbest, I.nv, c);
     gsync<GT>(c);
@@ -1166,7 +1231,7 @@ __device__ __forceinline__ void repair(const DevInst &I, const Ctx &c)
 // ---- PartialCol (Sec. 3.7): legal partial colourings only ------------------
 template <int NWC, int GT>
 __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs &a, const Ctx &c, uint32_t *G, uint8_t *gbest,
-                                 int slot, int ind, int64_t N, int span, LaneStats &st, long long &fbest_out)
+                                 int slot, int ind, int64_t N, int span, long long &fbest_out)
 {
     constexpr int W = Grp<GT>::W, NW = Grp<GT>::NW;
     build_planes<GT>(I, c);
@@ -1178,12 +1243,15 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
     tabu_reset<GT>(I, c);
     rebuild_list<GT>(I, c);
     Clock ck = claim_clock<GT>(I, a, c, G, slot, span);
-    const uint32_t ctr2 = ((uint32_t)a.gen << 8) | (kPurposeTabu << 4) | 3u;
     uint32_t Lr = 0, rotr = 0;
     bool ok = true;
     int *ulist = c.s.scal + 8;   // a legal colouring has at most 2 mates of one colour
-    for (long long t = 1; t <= N; ++t) {
+    IterCounters wc = {0u, 0u, 0u};
+    const int Nt = (int)N;                               // at most 2^30 (checked by the host)
+    int t = 1;
+    for (; t <= Nt; ++t) {
         if (f == 0) break;
+        if ((t & kFoldMask) == 0) fold_counters<GT>(c, wc);
         uint32_t trel = (uint32_t)(t - ck.shift);
         if (trel >= kRebaseAt) {
             gsync<GT>(c);
@@ -1196,6 +1264,7 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         if (len > 2 * f + 64) len = rebuild_list<GT>(I, c);
         const int q = (int)((t - 1) & (W - 1));
         if (q == 0) {
+            const uint32_t ctr2 = ((uint32_t)a.gen << 8) | (kPurposeTabu << 4) | 3u;   // phase 3: PartialCol
             const uint4 u = philox4x32_10(make_uint4((uint32_t)(t + c.gl), (uint32_t)ind, ctr2, 0u), a.key0, a.key1);
             Lr = bounded(u.x, (uint32_t)a.tenure_rand);
             rotr = bounded(u.y, (uint32_t)I.nv);
@@ -1211,7 +1280,7 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
             int pairs, iv;
             const int kv = low ? eval_vertex_low<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs, iv)
                                : eval_vertex<NWC>(I, c, G, ck, trel, v, 1, -1, A, pairs, iv);
-            st.pairs += pairs;
+            wc.pairs += (uint32_t)pairs;
             if (kv != INT_MAX) key = min(key, make_key(kv, v, rsh, I.nv, 0));
         };
         if constexpr (NW == 1) {
@@ -1232,9 +1301,11 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         int ncand;
         const unsigned long long best = group_best<GT>(c, (int)(t & 1), key, live, ncand);
         if (ncand != f) { ok = false; break; }
-        st.iterations += 1;
-        st.cand += ncand;
-        if (best == kNoKey) continue;
+        wc.cand += (uint32_t)ncand;
+        if (best == kNoKey) {
+            if (c.gt == 0) walk_totals(c)->moves -= 1;
+            continue;
+        }
 
         const int d = (int)(uint32_t)(best >> 32) - (1 << 30);
         const uint32_t blo = (uint32_t)best;
@@ -1295,16 +1366,17 @@ __device__ __forceinline__ bool partialcol_phase(const DevInst &I, const LSArgs 
         }
         gsync<GT>(c);
         if (c.s.scal[6]) { ok = false; break; }
-        if (c.gt == 0) st.uncolored += c.s.scal[5];
+        if (c.gt == 0) walk_totals(c)->uncolored += c.s.scal[5];
         f += d;
-        st.moves += 1;
-        if (c.gt == 0) st.deg += vertex_degree(I, c, v);
+        if (c.gt == 0) wc.deg += (uint32_t)vertex_degree(I, c, v);
         if (f < fbest) {
             fbest = f;
-            st.improvements += 1;
+            if (c.gt == 0) walk_totals(c)->improvements += 1;
             gcopy<GT>(gbest, c.s.S, I.nv, c);
         }
     }
+    fold_counters<GT>(c, wc);
+    count_iterations(c, t);
     gsync<GT>(c);
     gcopy<GT>(c.s.S, gbest, I.nv, c);
     gsync<GT>(c);
@@ -1364,19 +1436,19 @@ __device__ __forceinline__ void walk_loop(const DevInst &I, const LSArgs &a, int
         const uint8_t *gin = a.S_in + (size_t)wk * I.nv;
         uint8_t *gout = a.S_out + (size_t)wk * I.nv;
         gcopy<GT>(c.s.S, gin, I.nv, c);
+        if (c.gt == 0) *walk_totals(c) = WalkTotals{0, 0, 0, 0, 0, 0, 0};
         gsync<GT>(c);
 
-        LaneStats st = {0, 0, 0, 0, 0, 0, 0};
         long long Flast = 0;
         bool ok = true;
         if (a.flags & PLSE_LS_PARTIALCOL) {
             if (a.flags & PLSE_LS_REPAIR) repair<GT>(I, c);
-            ok = partialcol_phase<NWC, GT>(I, a, c, G, gout, slot, ind, a.iters1, a.span1, st, Flast);
+            ok = partialcol_phase<NWC, GT>(I, a, c, G, gout, slot, ind, a.iters1, a.span1, Flast);
         } else {
             if (a.flags & PLSE_LS_PHASE1)
-                ok = plits_phase<NWC, GT>(I, a, c, G, gout, slot, ind, 1, a.iters1, a.phi2_1, a.span1, st, Flast);
+                ok = plits_phase<NWC, GT>(I, a, c, G, gout, slot, ind, 1, a.iters1, a.phi2_1, a.span1, Flast);
             if (ok && (a.flags & PLSE_LS_PHASE2))
-                ok = plits_phase<NWC, GT>(I, a, c, G, gout, slot, ind, 2, a.iters2, a.phi2_2, a.span2, st, Flast);
+                ok = plits_phase<NWC, GT>(I, a, c, G, gout, slot, ind, 2, a.iters2, a.phi2_2, a.span2, Flast);
             if (ok && (a.flags & PLSE_LS_REPAIR)) repair<GT>(I, c);
         }
         gsync<GT>(c);
@@ -1385,19 +1457,19 @@ __device__ __forceinline__ void walk_loop(const DevInst &I, const LSArgs &a, int
         int z = 0;
         for (int q = c.gt; q < I.nv; q += GT) z += (c.s.S[q] == 0);
         const int fz = gsum<GT>(z, c);
-        const long long pairs = gsum64<GT>(st.pairs, c);
         if (c.gt == 0) {
             if (a.f_out) a.f_out[wk] = fz;
             if (a.F_out) a.F_out[wk] = Flast;
             if (a.stats) {
+                const WalkTotals w = *walk_totals(c);
                 plse_walk_stats s;
-                s.iterations = st.iterations;
-                s.moves = st.moves;
-                s.cand = st.cand;
-                s.pairs = pairs;
-                s.deg = st.deg;
-                s.improvements = st.improvements;
-                s.uncolored = st.uncolored;
+                s.iterations = w.iterations;
+                s.moves = w.moves;
+                s.cand = w.cand;
+                s.pairs = w.pairs;
+                s.deg = w.deg;
+                s.improvements = w.improvements;
+                s.uncolored = w.uncolored;
                 a.stats[wk] = s;
             }
         }
@@ -1412,7 +1484,7 @@ __global__ void __launch_bounds__(kMaxThreads<NWC>, NWC >= 3 ? 1 : 2) local_sear
     if (a.skip && *a.skip) return;
     load_instance(I, smem);
     __syncthreads();
-    walk_loop<NWC, GT, GT == 16>(I, a, walks, make_ctx<GT>(smem, I, a.s_smem != 0));
+    walk_loop<NWC, GT, GT == 16>(I, a, walks, make_ctx<NWC, GT>(smem, I, a.s_smem != 0));
 }
 
 // Several launches' worth of walks (one per job, e.g. the same generation of
@@ -1457,7 +1529,7 @@ local_search_multi_kernel(const LSJob *jobs, int njobs, int walks, int s_smem, u
         group_sync<GT>(g, gm);
         if (jd->a.skip && *jd->a.skip) continue;
         const DevInst &I = jd->I;
-        walk_loop<NWC, GT, false>(I, jd->a, walks, make_ctx_at<GT>(I, s_smem != 0, I.rc, I.allow_row, I.linelen, sb));
+        walk_loop<NWC, GT, false>(I, jd->a, walks, make_ctx_at<NWC, GT>(I, s_smem != 0, I.rc, I.allow_row, I.linelen, sb));
     }
 }
 
