@@ -181,10 +181,10 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # DRAM bytes per tabu move of local_search_kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a launch with walks as long
-# as the benchmark's (bench.py --ls-case 0.3 --pop 2432 --ls-iters 34300
-# --steps 1: 107.0 MB + 249.1 MB for 2.972e7 moves); scaled to a benchmark
+# as the benchmark's (bench.py --ls-case 0.3 --pop 3040 --ls-iters 34300
+# --steps 1: 190.5 MB + 364.6 MB for 3.7253e7 moves); scaled to a benchmark
 # launch by its moves.  None whenever the kernel has changed since the capture.
-LS_DRAM_BYTES_PER_MOVE = None   # the kernel changed after the last capture (11.98 B per move)
+LS_DRAM_BYTES_PER_MOVE = (190515968 + 364592384) / 37.2532e6   # 14.90 B per move
 
 
 def union_ms(intervals):
