@@ -197,3 +197,39 @@ def test_launch_shape_does_not_change_results(plse, oracle_mod, name, launch):
     for w in range(0, count, 3):
         So, Fo, sto = oracle_ls(I, P[w], 5 + w, 9, iters, 31, plse.LS_REPAIR | plse.LS_PARTIALCOL)
         assert np.array_equal(S[w], So) and F[w] == Fo
+
+
+# Orders on both sides of each 32-colour-word boundary (colours 0..n take
+# ceil((n + 1) / 32) words: n = 31 | 32, 63 | 64, 95 | 96) and the largest order
+# the library accepts (127), where a walk's colour words and its launch shape
+# (threads per block, registers, walks per SM) change.
+BOUNDARY_ORDERS = [(31, 0.6), (32, 0.6), (63, 0.7), (64, 0.7), (95, 0.8), (96, 0.8), (127, 0.85)]
+
+
+@pytest.mark.parametrize("n,r", BOUNDARY_ORDERS)
+def test_colour_word_boundaries_and_maximum_order(plse, oracle_mod, n, r):
+    import torch
+    grid = inputs.random_insertion(n, r, 100 + n)
+    G, I = plse.Instance(grid), oracle_mod.Instance(grid)
+    assert (G.nv, G.l, G.ub) == (I.nv, I.l, I.ub)
+    count = 12
+    P = I.init_population(count, 7)
+    out = empty((count, G.nv), torch.uint8)
+    G.init_population(count, 7, out)
+    assert np.array_equal(host(out), P)
+    iters = min(2 * I.nv, 1200)
+    flags = plse.LS_PHASE1 | plse.LS_PHASE2 | plse.LS_REPAIR
+    S, f, F, st = run_gpu_ls(plse, G, P, 1, 4, iters, 3, flags)
+    for w in range(count):
+        So, Fo, sto = oracle_ls(I, P[w], 1 + w, 4, iters, 3, flags)
+        assert np.array_equal(S[w], So), (n, w)
+        assert F[w] == Fo and f[w] == int((So == 0).sum())
+        assert st[w].tolist() == [sto[k] for k in FIELDS], (n, w)
+    if r >= 0.8:                                     # PartialCol (Sec. 3.7) at the same orders
+        flags = plse.LS_REPAIR | plse.LS_PARTIALCOL
+        S, f, F, st = run_gpu_ls(plse, G, P, 1, 4, iters, 3, flags)
+        for w in range(count):
+            So, Fo, sto = oracle_ls(I, P[w], 1 + w, 4, iters, 3, flags)
+            assert np.array_equal(S[w], So), (n, w)
+            assert F[w] == Fo
+            assert st[w].tolist() == [sto[k] for k in FIELDS], (n, w)

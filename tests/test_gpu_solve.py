@@ -124,3 +124,11 @@ def test_no_stop_at_bound_keeps_generating(plse, oracle_mod):
     assert res["score"] == ref["score"] == 100
     g = res["best_grid"]
     assert is_partial_latin(g) and int((g != 0).sum()) == 100
+
+
+def test_whole_run_at_the_maximum_order(plse, oracle_mod):
+    # n = 127, the largest order accepted: every step of the generation at four
+    # colour words, whole-run parity over three generations
+    grid = inputs.random_insertion(127, 0.85, 227)
+    res, ref = compare(plse, oracle_mod, grid, 8, 3, 400, 5)
+    assert res["generations"] >= 1
