@@ -1093,11 +1093,13 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
         f += (j == 0) - (i == 0);
         F2 += d2;
         bool bad = false;
+        int degv = 0;
         if (c.wg == 0) {
             const uint16_t rc = c.rc[v];
             const int r = rc >> 8, cc = rc & 255;
-            // v's tabu-cache entry, needed last (tabu_insert), loaded first
+            // v's tabu-cache entry and degree, needed last, loaded first
             const uint2 tcv = c.gl == 0 ? c.s.tc[v] : make_uint2(0u, 0u);
+            degv = (int)c.linelen[r] + (int)c.linelen[I.n + cc] - 2;
             // member-id XOR of (row r | column cc, colour i | j), read first so that
             // its latency overlaps the count updates: lane 0 row/i, 1 column/i,
             // 2 row/j, 3 column/j
@@ -1120,8 +1122,6 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
                 }
             }
             if (c.gl == 0) c.s.S[v] = (uint8_t)j;
-            if (c.gl < 4 && xk) c.s.xr[xidx] = (uint16_t)(xold ^ v);   // v leaves i, joins j
-            const int dh_tot = __reduce_add_sync(c.gm, dh);
             // counts of colours i and j on the moved row (lane 0) and column (lane 1)
             // after the move, packed i | j << 8: lane l reads line l & 1's, and lane
             // 0 also the column's
@@ -1157,13 +1157,19 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
                 }
             }
             list_append(c, want, u, len);
-            bad = __any_sync(c.gm, bad_mate);
+            if (c.gl < 4 && xk) c.s.xr[xidx] = (uint16_t)(xold ^ v);   // v leaves i, joins j
             if (c.gl == 0) {
                 const int newc = j ? (int)(cnt_j + (col_cnt >> 8) - 2 > 0) : 0;   // v's own status at j
                 if (j != 0 && !newc) atomicAnd(&c.s.cmask[v >> 5], ~(1u << (v & 31)));
                 dconf += newc - (i != 0 ? 1 : 0);
             }
-            dconf = __reduce_add_sync(c.gm, dconf);
+            // one reduction for three sums: the change of |C(S)| (|.| <= 6), of the
+            // number of counts >= 4 (|.| <= 4) and the inconsistent mates (<= 4)
+            const int packed3 = __reduce_add_sync(c.gm, dconf + 32 * dh + 1024 * (int)bad_mate);
+            dconf = ((packed3 + 16) & 31) - 16;
+            const int rest = (packed3 - dconf) >> 5;
+            const int dh_tot = ((rest + 16) & 31) - 16;
+            bad = rest - dh_tot != 0;
             if (c.gl == 0) {
                 const int k = f + nconf + dconf;
                 const int T = L + tenure_div(a, a.alpha_num * k);
@@ -1185,7 +1191,7 @@ __device__ __forceinline__ bool plits_phase(const DevInst &I, const LSArgs &a, c
             nconf = c.s.scal[4];
         }
         if (bad) { ok = false; break; }
-        if (c.gt == 0) wc.deg += (uint32_t)vertex_degree(I, c, v);
+        if (c.gt == 0) wc.deg += (uint32_t)degv;
         if (F2 < F2best) {
             F2best = F2;
             if (c.gt == 0) walk_totals(c)->improvements += 1;
