@@ -184,7 +184,7 @@ def measured_peaks():
 # as the benchmark's (bench.py --ls-case 0.3 --pop 3040 --ls-iters 34300
 # --steps 1: 190.5 MB + 364.6 MB for 3.7253e7 moves); scaled to a benchmark
 # launch by its moves.  None whenever the kernel has changed since the capture.
-LS_DRAM_BYTES_PER_MOVE = (190515968 + 364592384) / 37.2532e6   # 14.90 B per move
+LS_DRAM_BYTES_PER_MOVE = None   # the kernel changed after the last capture (14.90 B per move)
 
 
 def union_ms(intervals):

@@ -707,8 +707,20 @@ __device__ __forceinline__ int eval_special(const TabuView &tv, uint32_t trel, i
     // colour); a live one is tabu and admissible by aspiration only, which needs
     // 2dF < A, while 2dF >= base2 for every colour (s_j >= 0): the values are
     // needed only when base2 < A
-    const bool l0 = tv.c0 != 0u && tv.e0 >= trel && test_bit<NWC>(m, tv.c0);
-    const bool l1 = tv.c1 != 0u && tv.e1 >= trel && test_bit<NWC>(m, tv.c1);
+    // (the word of each cache colour is selected once, for the test and the clear;
+    // an empty entry, colour 255, selects no word)
+    uint32_t sel0[NWC], sel1[NWC];
+    word_masks<NWC>(tv.c0, sel0);
+    word_masks<NWC>(tv.c1, sel1);
+    const uint32_t b0 = 1u << (tv.c0 & 31u), b1 = 1u << (tv.c1 & 31u);
+    uint32_t w0 = 0u, w1 = 0u;
+#pragma unroll
+    for (int q = 0; q < NWC; ++q) {
+        w0 |= m[q] & sel0[q];
+        w1 |= m[q] & sel1[q];
+    }
+    const bool l0 = tv.c0 != 0u && tv.e0 >= trel && (w0 & b0) != 0u;
+    const bool l1 = tv.c1 != 0u && tv.e1 >= trel && (w1 & b1) != 0u;
     if ((l0 || l1) && base2 < A) {
 #pragma unroll
         for (int sx = 0; sx < 2; ++sx) {
@@ -719,9 +731,10 @@ __device__ __forceinline__ int eval_special(const TabuView &tv, uint32_t trel, i
             }
         }
     }
-    // out of m (a colour >= 128 clears nothing)
-    clear_bit<NWC>(m, l0 ? tv.c0 : 255u);
-    clear_bit<NWC>(m, l1 ? tv.c1 : 255u);
+    // out of m
+    const uint32_t k0 = l0 ? b0 : 0u, k1 = l1 ? b1 : 0u;
+#pragma unroll
+    for (int q = 0; q < NWC; ++q) m[q] &= ~((k0 & sel0[q]) | (k1 & sel1[q]));
     return best;
 }
 
@@ -767,7 +780,7 @@ __device__ __forceinline__ int eval_vertex_low(const DevInst &I, const Ctx &c, c
         cnt += __popc(m[q]);
     }
     pairs = cnt;                                   // |D(v)| - 1 scanned moves
-    if (i) clear_bit<NWC>(m, (uint32_t)i);
+    clear_bit<NWC>(m, (uint32_t)i);                // colour 0 is never in m: no-op when i = 0
     const TabuView tv = tabu_view(I, te, ck, trel, G, v);
     int best = eval_special<NWC>(tv, trel, i, base2, d2zero, mult, A, m,
                                  [&](uint32_t k) { return value3<NWC>(s0, s1, s2, k); });
@@ -871,7 +884,7 @@ __device__ __forceinline__ int eval_vertex(const DevInst &I, const Ctx &c, const
         cnt += __popc(m[q]);
     }
     pairs = cnt;                                   // |D(v)| - 1 scanned moves
-    if (i) clear_bit<NWC>(m, (uint32_t)i);
+    clear_bit<NWC>(m, (uint32_t)i);                // colour 0 is never in m: no-op when i = 0
     const TabuView tv = tabu_view(I, te, ck, trel, G, v);
     int best = eval_special<NWC>(tv, trel, i, base2, d2zero, mult, A, m,
                                  [&](uint32_t k) { return count_of(c, rl, (int)k) + count_of(c, cl, (int)k); });
