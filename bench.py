@@ -182,9 +182,9 @@ def measured_peaks():
 # DRAM bytes per tabu move of local_search_kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a launch with walks as long
 # as the benchmark's (bench.py --ls-case 0.3 --pop 3040 --ls-iters 34300
-# --steps 1: 190.5 MB + 364.6 MB for 3.7253e7 moves); scaled to a benchmark
+# --steps 1: 193.8 MB + 365.0 MB for 3.7253e7 moves); scaled to a benchmark
 # launch by its moves.  None whenever the kernel has changed since the capture.
-LS_DRAM_BYTES_PER_MOVE = None   # the kernel changed after the last capture (14.90 B per move)
+LS_DRAM_BYTES_PER_MOVE = (193757184 + 365008384) / 37.2530e6   # 15.00 B per move
 
 
 def union_ms(intervals):
