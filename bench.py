@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--serve-mem", type=float, default=1.0,
                     help="with --serve: device-memory budget of the server in GB")
     ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--serve-seq-sample", type=int, default=0, metavar="K",
+                    help="serve: run the sequential leg on K evenly spaced requests only "
+                         "(0 = all); served results are checked against those")
     return ap.parse_args()
 
 
@@ -662,7 +665,9 @@ def run_serve_case(args):
     uniform over {10..100}, r ~ U[0.3, 0.8], seeds 5000+k), --generations
     generations each with the optimality stop, phase-1 iterations 10 x empty
     cells, population by size (never by load).  Three measurements:
-      sequential  -- the same requests through plse_solve one after another;
+      sequential  -- the same requests through plse_solve one after another
+                     (--serve-seq-sample K: K evenly spaced ones, the rate taken
+                     from them);
       capacity    -- all requests submitted at once to one plse_server (closed
                      loop): the sustainable solves/s;
       open loop   -- Poisson arrivals at min(--rate, 0.8 x capacity) into a fresh
@@ -687,17 +692,24 @@ def run_serve_case(args):
         srv.poll(w, wait_ms=-1)
         return srv
 
-    # sequential plse_solve
+    # sequential plse_solve (all requests, or an evenly spaced sample of them)
     G = plse.Instance(inputs.tiny_n10())
     G.solve(32, 2, 100, 1)
     G.close()
+    k = args.serve_seq_sample
+    sample = list(range(len(grids))) if k <= 0 or k >= len(grids) else \
+        sorted({(q * len(grids)) // k for q in range(k)})
     t0 = time.perf_counter()
-    seq = []
-    for g, j in zip(grids, jobs):
-        H = plse.Instance(g)
-        seq.append(H.solve(*j, with_stats=True))
+    seq = {}
+    for q in sample:
+        H = plse.Instance(grids[q])
+        seq[q] = H.solve(*jobs[q], with_stats=True)
         H.close()
     t_seq = time.perf_counter() - t0
+    seq_rate = len(sample) / t_seq
+
+    def identical(results):
+        return all(same(results[q], seq[q]) for q in sample)
 
     # capacity: closed loop
     srv = new_server()
@@ -736,10 +748,10 @@ def run_serve_case(args):
         "case": "serve", "requests": args.requests, "generations": args.generations,
         "phase1_iters": "10 x empty cells", "population": "2^16 / empty cells, power of two in [32, 512]",
         "max_inflight": inflight, "mem_budget_bytes": budget,
-        "sequential": {"wall_s": round(t_seq, 3), "solves_per_s": round(len(grids) / t_seq, 3)},
+        "sequential": {"requests": len(sample), "wall_s": round(t_seq, 3), "solves_per_s": round(seq_rate, 3)},
         "capacity": {"wall_s": round(t_cap, 3), "solves_per_s": round(capacity, 3),
-                     "vs_sequential": round(t_seq / t_cap, 3),
-                     "identical_to_sequential": all(same(a, b) for a, b in zip(cap_res, seq)),
+                     "vs_sequential": round(capacity / seq_rate, 3),
+                     "identical_to_sequential": identical(cap_res),
                      "memory": cap_mem},
         "open_loop": {"rate_per_s": round(rate, 3), "requested_rate_per_s": args.rate, "ok": ok,
                       "wall_s": round(t_all, 3), "solves_per_s": round(ok / t_all, 3),
@@ -749,7 +761,7 @@ def run_serve_case(args):
                                      "max": round(float(lat.max()), 1)},
                       "queue_ms": {"p50": round(float(np.percentile(qms, 50)), 1),
                                    "p99": round(float(np.percentile(qms, 99)), 1)},
-                      "identical_to_sequential": all(same(a, b) for a, b in zip(res, seq)),
+                      "identical_to_sequential": identical(res),
                       "memory": mem},
         "generations_mean": round(float(np.mean([r["generations"] for r in res])), 2),
         "moves": sum(r["walks"]["moves"] for r in res),
