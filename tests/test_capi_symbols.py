@@ -47,6 +47,8 @@ def test_strerror_and_invalid_arguments_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.plse_create(0, None, ctypes.byref(h)) == -1          # rejected before any CUDA call
     assert lib.plse_create(200, None, ctypes.byref(h)) == -1
+    empty128 = (ctypes.c_int8 * (128 * 128))()                      # a valid grid one order too large
+    assert lib.plse_create(128, empty128, ctypes.byref(h)) == -1
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):
