@@ -233,3 +233,25 @@ def test_colour_word_boundaries_and_maximum_order(plse, oracle_mod, n, r):
             assert np.array_equal(S[w], So), (n, w)
             assert F[w] == Fo
             assert st[w].tolist() == [sto[k] for k in FIELDS], (n, w)
+
+
+def test_empty_inputs_are_no_ops(plse, oracle_mod):
+    # zero walks, an empty population and zero-row distance blocks succeed and
+    # write nothing (output buffers keep a sentinel)
+    import torch
+    grid = cases()["ri_n16_r06"]
+    G = plse.Instance(grid)
+    nv = G.nv
+    S = torch.full((4, nv), 7, dtype=torch.uint8, device="cuda")
+    out = torch.full((4, nv), 9, dtype=torch.uint8, device="cuda")
+    f = torch.full((4,), -5, dtype=torch.int32, device="cuda")
+    D = torch.full((4, 4), -3, dtype=torch.int32, device="cuda")
+    flags = plse.LS_PHASE1 | plse.LS_PHASE2 | plse.LS_REPAIR
+    G.local_search(S, out, 0, 0, 0, 100, 1, flags, f)
+    G.local_search_noalloc(S, out, 0, 0, 0, 100, 1, flags, f)
+    G.init_population(0, 1, out)
+    G.distances(S, 0, S, 4, D)
+    G.distances(S, 4, S, 0, D)
+    G.sync()
+    assert bool((out == 9).all()) and bool((f == -5).all()) and bool((D == -3).all())
+    assert bool((S == 7).all())
